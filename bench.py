@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of the SBIM traction update (Section 2.3, Eq. (SBI)) on GB300.
+
+Workload (default): one half-space, 1024 x 1024 periodic boundary, dx = 100 m,
+c_s = 3464 m/s, c_p = 6000 m/s, rho = 2670 kg/m^3, dt = 0.3 dx / c_p, history
+cutoff 4096 steps, float32 history with compensated accumulation.  The history
+is filled by running n_cut steps of seeded k^-2 boundary motion first (untimed),
+then W warm-up and K timed steps.  A step is one full sbim_step: forward FFT,
+history convolution, assembly, inverse FFT, traction epilogue.
+
+Metric: mode-history MACs per second, 5 complex-by-real MACs per (Fourier
+mode, lag) pair over the n3 (n1/2 + 1) half-spectrum modes and min(n+1, n_cut)
+lags.  The history (51.6 GB) is far larger than L2, so no flush is needed.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+Under torchrun (N > 1) every rank runs an independent replica of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2102_08756_gb300.synth import config_large, separable_history  # noqa: E402
+
+MACS_PER_PAIR = 5
+BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
+# DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
+# full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
+NCU_TRAFFIC = {"conv_src_sha1": None, "bytes_per_launch": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x2", "bf16"])
+    p.add_argument("--kahan", type=int, default=1)
+    p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
+    p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    c = config_large()
+    if args.n:
+        c.update(n1=args.n, n3=args.n, L1=args.n * 100.0, L3=args.n * 100.0)
+    if args.n_cut:
+        c["n_cut"] = args.n_cut
+    return c
+
+
+def workload_name(c, precision, kahan):
+    return (f"single half-space SBIM step, {c['n1']}x{c['n3']} boundary, dx=100 m, "
+            f"{c['n_cut']}-lag history, {precision} history"
+            + (" + Kahan accumulation" if kahan and precision != "fp64" else ""))
+
+
+def n_modes(c):
+    return c["n3"] * (c["n1"] // 2 + 1)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def conv_src_sha1():
+    p = os.path.join(ROOT, "paper_2102_08756_gb300", "csrc", "sbim_conv.cu")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+_TABLES = {}
+
+
+def oracle_sample(c, sample_modes, seed, side=1):
+    """A bounded sample of the workload for the FP64 oracle: ``sample_modes``
+    random Fourier modes with their full-history weights and a random
+    history of n_cut steps (the kernel table is built once per process)."""
+    from oracle.sbim_oracle import KernelTable, Material, ModeSet, trapezoid_weights
+    rng = np.random.default_rng(seed)
+    nh = c["n1"] // 2 + 1
+    pick = rng.choice(c["n3"] * nh, size=sample_modes, replace=False)
+    modes = ModeSet.build(c["n1"], c["n3"], c["L1"], c["L3"], r3=pick // nh, j1=pick % nh)
+    mat = Material(c["cs"], c["cp"], c["rho"])
+    L = c["n_cut"]
+    dT_max = np.sqrt(2.0) * np.pi / min(c["L1"] / c["n1"], c["L3"] / c["n3"]) * c["cs"] * c["dt"]
+    key = (mat.eta, L, round(dT_max, 12))
+    if key not in _TABLES:
+        _TABLES[key] = KernelTable(mat.eta, dT_max * L + 1)
+    kt = _TABLES[key]
+    dT = modes.q * c["cs"] * c["dt"]
+    w = np.stack([trapezoid_weights(d, L, kt) for d in dT], axis=1)
+    hist = rng.normal(size=(L, 3, sample_modes)) + 1j * rng.normal(size=(L, 3, sample_modes))
+    return dict(modes=modes, mat=mat, side=side, w=w, hist=hist, L=L, n=sample_modes)
+
+
+def time_oracle(sample, min_seconds=0.0):
+    """Run the oracle's per-mode operator (convolution + assembly, FP64, one
+    thread) on the sample until ``min_seconds`` elapsed; returns (MAC/s, s, reps)."""
+    from oracle.sbim_oracle import apply_modal_operator
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        apply_modal_operator(sample["modes"], sample["mat"], sample["side"], sample["w"],
+                             sample["hist"], sample["hist"][0])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return sample["n"] * sample["L"] * MACS_PER_PAIR * reps / el, el, reps
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    c = workload(args)
+    sample = oracle_sample(c, sample_modes=256, seed=100)
+    for _ in range(args.warmup):
+        time_oracle(sample)
+    rates = [time_oracle(sample)[0] for _ in range(args.steps)]
+    value = float(np.mean(rates))
+    desc = (f"{sample['n']} random modes x {sample['L']} lags per step: the oracle's full-history "
+            f"per-mode operator, {args.steps} steps")
+    line = {
+        "impl": "reference", "metric": "SBIM mode-history MACs/s", "value": value, "unit": "MAC/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * n_modes(c) * c["n_cut"] * MACS_PER_PAIR / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(c, "fp64", 0) + " (FP64 CPU oracle, sampled modes)",
+                   "n1": c["n1"], "n3": c["n3"], "n_cut": c["n_cut"]},
+        "cpu_baseline": {"value": value, "unit": "MAC/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2102_08756_gb300 import _build
+    _build.build()
+    from paper_2102_08756_gb300.sbim import SBIM
+
+    c = workload(args)
+    n1, n3, n_cut, dt = c["n1"], c["n3"], c["n_cut"], c["dt"]
+    prec = args.precision
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    stream = torch.cuda.current_stream()
+    g = SBIM(n1, n3, c["L1"], c["L3"], c["cs"], c["cp"], c["rho"], dt, n_cut, 1, prec,
+             bool(args.kahan), stream=stream)
+    K, W = args.steps, args.warmup
+    total_steps = n_cut + W + K
+    hist = separable_history(n1, n3, c["L1"], c["L3"], total_steps + 1, dt, c["cs"],
+                             seed=1000 * 3 + rank, n_terms=4, spectrum="k2")
+    U = torch.from_numpy(hist.U).to(dev, tdt)
+    gts = torch.from_numpy(hist.g).to(tdt)
+    u = torch.empty((3, n3, n1), device=dev, dtype=tdt)
+    v = torch.empty_like(u)
+    tau = torch.empty_like(u)
+
+    def fields(m, out_u, out_v):
+        torch.mul(U[0], float(gts[0, m]), out=out_u)
+        for r in range(1, U.shape[0]):
+            out_u.add_(U[r], alpha=float(gts[r, m]))
+        gp = gts[:, m - 1] if m > 0 else torch.zeros_like(gts[:, 0])
+        dg = (gts[:, m] - gp) / dt
+        torch.mul(U[0], float(dg[0]), out=out_v)
+        for r in range(1, U.shape[0]):
+            out_v.add_(U[r], alpha=float(dg[r]))
+
+    # fill the history (untimed)
+    for m in range(n_cut):
+        fields(m, u, v)
+        g.step(u, v, tau)
+    # inputs of the warm-up and timed steps, resident in HBM before timing
+    us = [torch.empty_like(u) for _ in range(W + K)]
+    vs = [torch.empty_like(u) for _ in range(W + K)]
+    for k in range(W + K):
+        fields(n_cut + k, us[k], vs[k])
+    for k in range(W):
+        g.step(us[k], vs[k], tau)
+    torch.cuda.synchronize()
+
+    g.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)                       # let the sampler start
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(stream)
+        for k in range(W, W + K):
+            g.step(us[k], vs[k], tau)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    stage, nprof = g.stage_times()
+    g.set_profiling(False)
+    hist_bytes = g.info()["hist_bytes"]
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    modes = n_modes(c)
+    L = n_cut
+    macs_step = modes * L * MACS_PER_PAIR
+    value = world * macs_step / (ms_step * 1e-3)
+
+    # roofline of the convolution kernel (algorithmic bytes per launch)
+    conv_ms = stage["convolution"] / nprof
+    bpp = BYTES_PER_PAIR[prec]
+    alg_bytes = modes * (L + 1) * bpp
+    achieved = alg_bytes / (conv_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    if NCU_TRAFFIC["conv_src_sha1"] == conv_src_sha1() and prec == "fp32" and n1 == 1024 \
+            and n_cut == 4096:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty((3, n3, n1), dtype=tdt, pin_memory=True)
+        hv = torch.empty_like(hu).pin_memory()
+        ht = torch.empty_like(hu).pin_memory()
+        hu.copy_(us[-1].cpu())
+        hv.copy_(vs[-1].cpu())
+        from paper_2102_08756_gb300 import sbim as B
+        for _ in range(2):
+            B.sbim_step_host(g.h, hu.data_ptr(), hv.data_ptr(), ht.data_ptr())
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            B.sbim_step_host(g.h, hu.data_ptr(), hv.data_ptr(), ht.data_ptr())
+        t1 = time.perf_counter()
+        e2e_s = (t1 - t0) / K
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        fb = hu.numel() * hu.element_size()
+        e2e = {"value": world * macs_step / e2e_s, "unit": "MAC/s",
+               "h2d_bytes_per_step": 2 * fb, "d2h_bytes_per_step": fb,
+               "ms_per_step": e2e_s * 1e3}
+    g.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        smp = oracle_sample(c, sample_modes=1024, seed=7)
+        rate, secs, reps = time_oracle(smp, min_seconds=10.0)
+        cpu = {"value": rate, "unit": "MAC/s", "cores": 1, "kind": "oracle",
+               "sample": (f"{smp['n']} random modes x {smp['L']} lags of the full-history "
+                          f"per-mode operator, repeated {reps}x ({secs:.1f} s, one thread)")}
+    line = {
+        "metric": "SBIM mode-history MACs/s", "value": value, "unit": "MAC/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": workload_name(c, prec, args.kahan), "n1": n1, "n3": n3,
+                   "n_cut": n_cut, "precision": prec, "kahan": int(bool(args.kahan)),
+                   "modes": modes, "history_bytes": hist_bytes,
+                   "l2": "inputs larger than L2 (history ring buffer >> 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "conv_kernel", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": conv_ms},
+        "stage_ms_per_step": {k: v / nprof for k, v in stage.items()},
+        "hbm_gbs_step": alg_bytes / (ms_step * 1e-3) / 1e9,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * K,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

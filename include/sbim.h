@@ -1,0 +1,154 @@
+/*
+ * sbim.h -- C ABI of the GB300 spectral-boundary-integral (SBIM) traction update.
+ *
+ * The operation (Albertini, Elbanna & Kammer, Section 2.3, Eq. (SBI)) maps the
+ * displacement history and current velocity of the boundary plane of one elastic
+ * half-space to the traction on that plane:
+ *
+ *     tau_i = tau_i^inf - eta_ij (mu / c_s) du_j/dt + s_i ,
+ *
+ * with eta_ij = diag(1, c_p/c_s, 1), mu = rho c_s^2, and s_i the non-local term
+ * evaluated spectrally (Section 2.3, "spectral approach"): a 2D Fourier transform
+ * of the three displacement components over the periodic boundary plane, a
+ * truncated time convolution of every Fourier mode's history with the half-space
+ * kernels H11, H22, H33, H12(|k| c_s t), and an inverse transform.  One call of
+ * sbim_step is step 3 of the hybrid time step of Section 2.4 for one half-space
+ * (S+ or S-).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an sbim_status; 0 is success.  On failure the
+ *     calling thread's message is available from sbim_last_error().  Output
+ *     arguments are written only on success.
+ *   - Fields are row-major [3][n3][n1] arrays (component, x3, x1 with x1
+ *     fastest), in SI units (m, m/s, Pa).  The component index is the Cartesian
+ *     direction 1, 2, 3 of the paper, x2 being the normal of the boundary.
+ *   - Element type: double for SBIM_FP64 handles, float for every other precision.
+ *   - A handle owns all its device memory (history ring buffer, kernel tables,
+ *     FFT plans, work buffers), is bound to one CUDA stream, and must not be used
+ *     from two threads at once.
+ */
+#ifndef SBIM_H
+#define SBIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbim_ctx* sbim_handle;
+
+typedef enum {
+    SBIM_OK = 0,
+    SBIM_ERR_ARG = -1,       /* invalid argument (value, pointer, alignment, size) */
+    SBIM_ERR_OOM = -2,       /* device or host allocation failed / would not fit */
+    SBIM_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    SBIM_ERR_FFT = -4,       /* a cuFFT call failed */
+    SBIM_ERR_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+    SBIM_ERR_NONFINITE = -6, /* reserved: non-finite input detected */
+    SBIM_ERR_STATE = -7      /* call not valid in the handle's current state */
+} sbim_status;
+
+typedef enum {
+    SBIM_FP64 = 0,   /* history and arithmetic in double; I/O double */
+    SBIM_FP32 = 1,   /* history float, accumulation float (optionally compensated) */
+    SBIM_BF16X2 = 2, /* history as bf16 hi + bf16 lo per real, float accumulation */
+    SBIM_BF16 = 3    /* history as bf16 hi only, float accumulation */
+} sbim_precision;
+
+/*
+ * sbim_create -- build a handle for one half-space.
+ *
+ * Section 2.3 (problem statement of Eq. (SBI)) and Section 2.4 (the boundary S+
+ * or S- of the finite-element strip).
+ *   n1, n3     grid points along x1 and x3 (even, >= 2); periodic boundary plane
+ *   L1, L3     periodic lengths (m), grid spacing L1/n1, L3/n3
+ *   cs, cp     shear and dilatational wave speeds (m/s), cp > cs > 0
+ *   rho        density (kg/m^3) > 0
+ *   dt         time step (s) > 0, the spacing of consecutive sbim_step calls
+ *   n_cut      history cutoff in steps (>= 1): the convolution uses the last
+ *              min(n+1, n_cut) displacement fields, the current one included
+ *   side       +1: half-space x2 > boundary (material above the plane, S+);
+ *              -1: half-space x2 < boundary (S-)
+ *   precision  an sbim_precision value
+ *   kahan      non-zero: compensated (Kahan) float accumulation over the lags
+ *              (ignored for SBIM_FP64)
+ *   stream     cudaStream_t every call of this handle is ordered on; NULL = the
+ *              legacy default stream
+ * The kernel tables are built on the device in double precision.  Returns
+ * SBIM_ERR_OOM if the history ring buffer (n_cut x 3 x modes, complex) does not
+ * fit in free device memory.  *out is written on success only.
+ */
+int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3,
+                double cs, double cp, double rho, double dt, int n_cut,
+                int side, int precision, int kahan, void* stream);
+
+/*
+ * sbim_step -- one traction evaluation, Eq. (SBI), at the next time step n.
+ *
+ *   u    device pointer, displacement of the boundary at step n      [3][n3][n1]
+ *   v    device pointer, velocity at step n (Section 2.4: the FE predicted
+ *        velocity), used only by the radiation-damping term          [3][n3][n1]
+ *   tau  device pointer, output traction sigma_2i on the boundary    [3][n3][n1]
+ * u is appended to the handle's history (step 0 is the first call after
+ * sbim_create or sbim_reset; earlier displacements are zero).  The call is
+ * asynchronous and ordered on the handle's stream; the caller keeps u, v, tau
+ * alive until the stream has passed them.  u, v and tau must not overlap.
+ */
+int sbim_step(sbim_handle h, const void* u, const void* v, void* tau);
+
+/*
+ * sbim_step_host -- as sbim_step, with u, v, tau in HOST memory (pageable or
+ * pinned).  Copies the inputs to device work buffers, runs the step, copies
+ * tau back and waits for the stream.  Section 2.4 step 2 ("copy u and the
+ * predicted velocity from FE to SBI") for a caller whose FE solver runs on the
+ * host.
+ */
+int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau);
+
+/*
+ * sbim_set_far_field -- tau_i^inf of Eq. (SBI) (Pa), a uniform far-field
+ * traction added to every output; default (0, 0, 0).
+ */
+int sbim_set_far_field(sbim_handle h, const double tau_inf[3]);
+
+/* sbim_reset -- forget the history; the next sbim_step is step 0 again. */
+int sbim_reset(sbim_handle h);
+
+/* sbim_get_step -- number of sbim_step calls since creation or the last reset. */
+int sbim_get_step(sbim_handle h, long long* n);
+
+/*
+ * sbim_get_info -- sizes of the handle's spectral work, for throughput
+ * accounting.  Any pointer may be NULL.
+ *   n_modes     half-spectrum Fourier bins, n3 (n1/2 + 1)
+ *   n_slots     storage slots per history step: equal-|k| groups x 4 members
+ *               (Nyquist bins count twice or four times, padding included)
+ *   hist_bytes  bytes of the history ring buffer
+ *   table_nodes entries of the interpolated kernel table
+ */
+int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
+                  long long* hist_bytes, long long* table_nodes);
+
+/*
+ * sbim_set_profiling / sbim_stage_times -- per-stage device time.  While
+ * profiling is on, every sbim_step records CUDA events on the handle's stream
+ * around its stages; sbim_stage_times waits for them and returns the summed
+ * milliseconds of (0) forward FFT, (1) history convolution, (2) reduction and
+ * assembly, (3) inverse FFT, (4) traction epilogue, and the number of steps
+ * summed.  Enabling clears the sums.
+ */
+int sbim_set_profiling(sbim_handle h, int enable);
+int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
+
+/* sbim_destroy -- free everything the handle owns; NULL is accepted. */
+int sbim_destroy(sbim_handle h);
+
+/* sbim_last_error -- message of the calling thread's last failure ("" if none). */
+const char* sbim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBIM_H */

@@ -1,0 +1,578 @@
+// Host side of libsbim: the C ABI declared in include/sbim.h.
+//
+// sbim_create plans the spectral layout (|k|-sorted orbits of Fourier-bin
+// members, Section 2.3 spectral evaluation of s_i), builds the kernel tables
+// on the device in FP64, allocates the history ring buffer and creates the
+// cuFFT plans.  sbim_step enqueues, on the handle's stream:
+//   (0) R2C FFT of u                      (cuFFT)
+//   (1) rotate + ring write + convolution  conv_kernel
+//   (2) chunk reduction + assembly         assemble_kernel
+//   (3) C2R FFT of the traction spectra    (cuFFT)
+//   (4) traction epilogue                  epilogue_kernel
+// with no host synchronisation.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sbim.h"
+#include "sbim_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+const char* fft_name(cufftResult r) {
+  switch (r) {
+    case CUFFT_SUCCESS: return "CUFFT_SUCCESS";
+    case CUFFT_INVALID_PLAN: return "CUFFT_INVALID_PLAN";
+    case CUFFT_ALLOC_FAILED: return "CUFFT_ALLOC_FAILED";
+    case CUFFT_INVALID_VALUE: return "CUFFT_INVALID_VALUE";
+    case CUFFT_INTERNAL_ERROR: return "CUFFT_INTERNAL_ERROR";
+    case CUFFT_EXEC_FAILED: return "CUFFT_EXEC_FAILED";
+    case CUFFT_SETUP_FAILED: return "CUFFT_SETUP_FAILED";
+    case CUFFT_INVALID_SIZE: return "CUFFT_INVALID_SIZE";
+    default: return "cuFFT error";
+  }
+}
+
+#define CU(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(e_ == cudaErrorMemoryAllocation ? SBIM_ERR_OOM : SBIM_ERR_CUDA,   \
+                  "%s: %s", #call, cudaGetErrorString(e_));                        \
+  } while (0)
+
+#define CF(call)                                                                   \
+  do {                                                                             \
+    cufftResult r_ = (call);                                                       \
+    if (r_ != CUFFT_SUCCESS) return fail(SBIM_ERR_FFT, "%s: %s", #call, fft_name(r_)); \
+  } while (0)
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kProfRing = 512;
+constexpr int kProfEvents = 6;
+
+// 16-point Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_16).
+void gauss_legendre16(double* x, double* w) {
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+struct Member {
+  int bin;
+  double e1, e3;
+  float w;
+};
+
+}  // namespace
+
+struct sbim_ctx {
+  int n1 = 0, n3 = 0, nh = 0, nbins = 0, n_cut = 0, side = 1, prec = SBIM_FP32, kahan = 0;
+  double L1 = 0, L3 = 0, cs = 0, cp = 0, rho = 0, dt = 0, mu = 0, eta = 0;
+  cudaStream_t stream = nullptr;
+  int n_orb = 0, n_orb_pad = 0, lc = 1, nchunks = 1;
+  double tab_h = 0;
+  long long tab_n = 0;
+  size_t real_size = 4;
+
+  int* d_bin = nullptr;
+  void* d_dir = nullptr;  // float2, or double2 for the FP64 path
+  float* d_wout = nullptr;
+  void* d_dT = nullptr;
+  unsigned long long* d_ustep = nullptr;
+  void* d_muq = nullptr;
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_gl = nullptr;
+  void* d_hist = nullptr;
+  size_t hist_bytes = 0;
+  long long plane_records = 0;
+  void* d_part = nullptr;
+  void* d_uhat = nullptr;
+  void* d_fhat = nullptr;
+  void* d_s = nullptr;
+  long long* d_step = nullptr;
+  void* d_io = nullptr;  // u, v, tau staging for sbim_step_host
+  cufftHandle plan_fwd = 0, plan_inv = 0;
+  bool have_fwd = false, have_inv = false;
+
+  long long n = 0;
+  double tau_inf[3] = {0, 0, 0};
+
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;      // kProfRing * kProfEvents
+  long long prof_issued = 0, prof_harvested = 0;
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+
+  size_t field_elems() const { return (size_t)3 * n1 * n3; }
+};
+
+namespace {
+
+// Group the half-spectrum bins into |k|-sorted orbits of <= 4 members.
+void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_orb) {
+  const bool square = (c.n1 == c.n3) && (c.L1 == c.L3);
+  struct Rec {
+    long long ikey;
+    double dkey;
+    int j1, r3, j3;
+  };
+  std::vector<Rec> recs;
+  recs.reserve(c.nbins);
+  for (int r3 = 0; r3 < c.n3; ++r3) {
+    const int j3 = r3 <= c.n3 / 2 ? r3 : r3 - c.n3;
+    for (int j1 = 0; j1 < c.nh; ++j1) {
+      Rec r;
+      r.j1 = j1;
+      r.r3 = r3;
+      r.j3 = j3;
+      r.ikey = square ? (long long)j1 * j1 + (long long)j3 * j3 : 0;
+      const double a = j1 / c.L1, b = j3 / c.L3;
+      r.dkey = a * a + b * b;
+      recs.push_back(r);
+    }
+  }
+  auto less = [square](const Rec& x, const Rec& y) {
+    if (square) {
+      if (x.ikey != y.ikey) return x.ikey < y.ikey;
+    } else if (x.dkey != y.dkey) {
+      return x.dkey < y.dkey;
+    }
+    if (x.j1 != y.j1) return x.j1 < y.j1;
+    return x.r3 < y.r3;
+  };
+  std::sort(recs.begin(), recs.end(), less);
+  auto same = [square](const Rec& x, const Rec& y) {
+    return square ? x.ikey == y.ikey : x.dkey == y.dkey;
+  };
+
+  std::vector<Member> cur;
+  auto flush = [&](double q) {
+    if (cur.empty()) return;
+    while (cur.size() < 4) cur.push_back(Member{-1, 1.0, 0.0, 0.0f});
+    mem.insert(mem.end(), cur.begin(), cur.end());
+    q_orb.push_back(q);
+    cur.clear();
+  };
+  size_t i = 0;
+  while (i < recs.size()) {
+    size_t j = i;
+    while (j < recs.size() && same(recs[i], recs[j])) ++j;
+    const double k1c = 2.0 * kPi * recs[i].j1 / c.L1, k3c = 2.0 * kPi * recs[i].j3 / c.L3;
+    const double q = std::hypot(k1c, k3c);
+    for (size_t t = i; t < j; ++t) {
+      const Rec& r = recs[t];
+      const bool ny1 = (r.j1 == c.n1 / 2), ny3 = (r.r3 == c.n3 / 2);
+      const double k1 = 2.0 * kPi * r.j1 / c.L1, k3 = 2.0 * kPi * r.j3 / c.L3;
+      const int bin = r.r3 * c.nh + r.j1;
+      std::vector<Member> grp;
+      const int n_s1 = ny1 ? 2 : 1, n_s3 = ny3 ? 2 : 1;
+      const float wgt = 1.0f / (float)(n_s1 * n_s3);
+      for (int a = 0; a < n_s1; ++a)
+        for (int b = 0; b < n_s3; ++b) {
+          const double s1 = a ? -1.0 : 1.0, s3 = b ? -1.0 : 1.0;
+          Member m;
+          m.bin = bin;
+          if (q > 0) {
+            m.e1 = s1 * k1 / q;
+            m.e3 = s3 * k3 / q;
+            m.w = wgt;
+          } else {  // k = 0 carries no non-local traction
+            m.e1 = 1.0;
+            m.e3 = 0.0;
+            m.w = 0.0f;
+          }
+          grp.push_back(m);
+        }
+      if (cur.size() + grp.size() > 4) flush(q);
+      cur.insert(cur.end(), grp.begin(), grp.end());
+    }
+    flush(q);
+    i = j;
+  }
+}
+
+int choose_chunks(sbim_ctx& c) {
+  int dev = 0, sms = 148;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long tiles = c.n_orb_pad / sbim::kOrbitTile;
+  const long long target = (long long)sms * 3 * 16;
+  long long S = (target + tiles - 1) / tiles;
+  const long long smax = std::max(1, (c.n_cut + 15) / 16);
+  S = std::max(1LL, std::min(S, smax));
+  c.lc = (int)((c.n_cut + S - 1) / S);
+  c.nchunks = (c.n_cut + c.lc - 1) / c.lc;
+  return SBIM_OK;
+}
+
+void release(sbim_ctx* c) {
+  if (!c) return;
+  if (c->have_fwd) cufftDestroy(c->plan_fwd);
+  if (c->have_inv) cufftDestroy(c->plan_inv);
+  void* ptrs[] = {c->d_bin, c->d_dir, c->d_wout, c->d_dT, c->d_ustep, c->d_muq,
+                  c->d_tab64, c->d_tab32, c->d_gl, c->d_hist, c->d_part, c->d_uhat,
+                  c->d_fhat, c->d_s, c->d_step, c->d_io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
+
+int harvest(sbim_ctx* c, long long upto) {
+  while (c->prof_harvested < upto) {
+    cudaEvent_t* e = &c->ev[(c->prof_harvested % kProfRing) * kProfEvents];
+    CU(cudaEventSynchronize(e[kProfEvents - 1]));
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e[k], e[k + 1]));
+      c->prof_ms[k] += ms;
+    }
+    ++c->prof_harvested;
+  }
+  return SBIM_OK;
+}
+
+int create_impl(sbim_ctx* c) {
+  c->mu = c->rho * c->cs * c->cs;
+  c->eta = c->cp / c->cs;
+  c->nh = c->n1 / 2 + 1;
+  c->nbins = c->n3 * c->nh;
+  const bool dbl = c->prec == SBIM_FP64;
+  c->real_size = dbl ? 8 : 4;
+
+  std::vector<Member> mem;
+  std::vector<double> q_orb;
+  plan_orbits(*c, mem, q_orb);
+  c->n_orb = (int)q_orb.size();
+  c->n_orb_pad = (c->n_orb + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
+  mem.resize((size_t)c->n_orb_pad * 4, Member{-1, 1.0, 0.0, 0.0f});
+  q_orb.resize(c->n_orb_pad, 0.0);
+
+  // kernel-table resolution: cubic interpolation error ~ 0.0234 h^4 max|H''''|
+  c->tab_h = dbl ? 1.0 / 512.0 : 1.0 / 64.0;
+  double dT_max = 0.0;
+  std::vector<double> dT(c->n_orb_pad), muq(c->n_orb_pad);
+  std::vector<unsigned long long> ustep(c->n_orb_pad);
+  for (int o = 0; o < c->n_orb_pad; ++o) {
+    dT[o] = q_orb[o] * c->cs * c->dt;
+    muq[o] = c->mu * q_orb[o];
+    dT_max = std::max(dT_max, dT[o]);
+    ustep[o] = (unsigned long long)std::llround(dT[o] / c->tab_h * 4294967296.0);
+  }
+  const double t_max = dT_max * (c->n_cut - 1);
+  c->tab_n = (long long)std::floor(t_max / c->tab_h) + 6;  // nodes -1 .. floor + 4
+  if ((double)c->n_cut * (dT_max / c->tab_h + 1.0) * 4294967296.0 > 1.8e19 ||
+      c->tab_n > (1LL << 31))
+    return fail(SBIM_ERR_ARG, "history too long for the kernel table (n_cut x |k|max c_s dt)");
+
+  std::vector<int> h_bin(mem.size());
+  std::vector<float2> h_dir(mem.size());
+  std::vector<double2> h_dir64(mem.size());
+  std::vector<float> h_w(mem.size());
+  for (size_t i = 0; i < mem.size(); ++i) {
+    h_bin[i] = mem[i].bin;
+    h_dir[i] = make_float2((float)mem[i].e1, (float)mem[i].e3);
+    h_dir64[i] = make_double2(mem[i].e1, mem[i].e3);
+    h_w[i] = mem[i].w;
+  }
+
+  if (choose_chunks(*c) != SBIM_OK) return SBIM_ERR_CUDA;
+
+  // history size
+  long long rec_bytes = 0;
+  int planes = 1;
+  switch (c->prec) {
+    case SBIM_FP64: rec_bytes = 64; break;
+    case SBIM_FP32: rec_bytes = 32; break;
+    case SBIM_BF16X2: rec_bytes = 16; planes = 2; break;
+    case SBIM_BF16: rec_bytes = 16; break;
+  }
+  c->plane_records = (long long)c->n_cut * 3 * c->n_orb_pad;
+  c->hist_bytes = (size_t)c->plane_records * rec_bytes * planes;
+  const size_t part_bytes = (size_t)c->nchunks * 4 * sbim::kFields * c->n_orb_pad * c->real_size;
+  const size_t cplx = 2 * c->real_size;
+  size_t free_b = 0, total_b = 0;
+  CU(cudaMemGetInfo(&free_b, &total_b));
+  const size_t need = c->hist_bytes + part_bytes + 2 * 3 * (size_t)c->nbins * cplx +
+                      4 * c->field_elems() * c->real_size + (size_t)c->tab_n * 48;
+  if (need + (256ull << 20) > free_b)
+    return fail(SBIM_ERR_OOM, "need %.2f GB of device memory, %.2f GB free",
+                need / 1e9, free_b / 1e9);
+
+  CU(cudaMalloc(&c->d_bin, h_bin.size() * sizeof(int)));
+  CU(cudaMalloc(&c->d_dir, h_dir.size() * (dbl ? sizeof(double2) : sizeof(float2))));
+  CU(cudaMalloc(&c->d_wout, h_w.size() * sizeof(float)));
+  CU(cudaMalloc(&c->d_dT, c->n_orb_pad * c->real_size));
+  CU(cudaMalloc(&c->d_muq, c->n_orb_pad * c->real_size));
+  CU(cudaMalloc(&c->d_ustep, c->n_orb_pad * sizeof(unsigned long long)));
+  CU(cudaMalloc(&c->d_tab64, (size_t)c->tab_n * 4 * sizeof(double)));
+  if (!dbl) CU(cudaMalloc(&c->d_tab32, (size_t)c->tab_n * 4 * sizeof(float)));
+  CU(cudaMalloc(&c->d_gl, 32 * sizeof(double)));
+  CU(cudaMalloc(&c->d_hist, c->hist_bytes));
+  CU(cudaMalloc(&c->d_part, part_bytes));
+  CU(cudaMalloc(&c->d_uhat, 3 * (size_t)c->nbins * cplx));
+  CU(cudaMalloc(&c->d_fhat, 3 * (size_t)c->nbins * cplx));
+  CU(cudaMalloc(&c->d_s, c->field_elems() * c->real_size));
+  CU(cudaMalloc(&c->d_step, sizeof(long long)));
+
+  cudaStream_t st = c->stream;
+  CU(cudaMemcpyAsync(c->d_bin, h_bin.data(), h_bin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (dbl)
+    CU(cudaMemcpyAsync(c->d_dir, h_dir64.data(), h_dir64.size() * sizeof(double2),
+                       cudaMemcpyHostToDevice, st));
+  else
+    CU(cudaMemcpyAsync(c->d_dir, h_dir.data(), h_dir.size() * sizeof(float2),
+                       cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(c->d_wout, h_w.data(), h_w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(c->d_ustep, ustep.data(), ustep.size() * sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, st));
+  if (dbl) {
+    CU(cudaMemcpyAsync(c->d_dT, dT.data(), dT.size() * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(c->d_muq, muq.data(), muq.size() * 8, cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float> f1(dT.begin(), dT.end()), f2(muq.begin(), muq.end());
+    CU(cudaMemcpyAsync(c->d_dT, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(c->d_muq, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));  // f1, f2 leave scope
+  }
+  double gl[32];
+  gauss_legendre16(gl, gl + 16);
+  CU(cudaMemcpyAsync(c->d_gl, gl, sizeof gl, cudaMemcpyHostToDevice, st));
+  CU(sbim::launch_table_build(c->d_tab64, c->d_tab32, c->tab_n, c->tab_h, c->eta, c->d_gl,
+                              c->d_gl + 16, st));
+  CU(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
+  CU(cudaStreamSynchronize(st));
+
+  // cuFFT plans: batch of 3 components, [n3][n1] real <-> [n3][n1/2+1] complex
+  int dims[2] = {c->n3, c->n1};
+  CF(cufftPlanMany(&c->plan_fwd, 2, dims, nullptr, 1, c->n3 * c->n1, nullptr, 1, c->nbins,
+                   dbl ? CUFFT_D2Z : CUFFT_R2C, 3));
+  c->have_fwd = true;
+  CF(cufftPlanMany(&c->plan_inv, 2, dims, nullptr, 1, c->nbins, nullptr, 1, c->n3 * c->n1,
+                   dbl ? CUFFT_Z2D : CUFFT_C2R, 3));
+  c->have_inv = true;
+  CF(cufftSetStream(c->plan_fwd, st));
+  CF(cufftSetStream(c->plan_inv, st));
+  return SBIM_OK;
+}
+
+sbim::StepArgs step_args(const sbim_ctx* c) {
+  sbim::StepArgs a;
+  a.bin = c->d_bin;
+  a.dir = c->d_dir;
+  a.wout = c->d_wout;
+  a.dT = c->d_dT;
+  a.ustep = c->d_ustep;
+  a.muq = c->d_muq;
+  a.table = c->prec == SBIM_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
+  a.hist = c->d_hist;
+  a.step = c->d_step;
+  a.part = c->d_part;
+  a.uhat = c->d_uhat;
+  a.fhat = c->d_fhat;
+  a.n_orb_pad = c->n_orb_pad;
+  a.nbins = c->nbins;
+  a.n_cut = c->n_cut;
+  a.lc = c->lc;
+  a.nchunks = c->nchunks;
+  a.side = c->side;
+  a.eta = c->eta;
+  a.inv_n = 1.0 / ((double)c->n1 * c->n3);
+  a.slot_stride = c->plane_records;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double cs, double cp,
+                double rho, double dt, int n_cut, int side, int precision, int kahan,
+                void* stream) {
+  g_err.clear();
+  if (!out) return fail(SBIM_ERR_ARG, "out is NULL");
+  if (n1 < 2 || n3 < 2 || (n1 & 1) || (n3 & 1))
+    return fail(SBIM_ERR_ARG, "n1 and n3 must be even and >= 2 (got %d, %d)", n1, n3);
+  if ((long long)n1 * n3 > (1LL << 28)) return fail(SBIM_ERR_ARG, "grid too large");
+  if (!(L1 > 0) || !(L3 > 0) || !(dt > 0) || !(rho > 0) || !(cs > 0))
+    return fail(SBIM_ERR_ARG, "L1, L3, dt, rho and cs must be positive");
+  if (!(cp > cs)) return fail(SBIM_ERR_ARG, "cp must exceed cs");
+  if (n_cut < 1) return fail(SBIM_ERR_ARG, "n_cut must be >= 1");
+  if (side != 1 && side != -1) return fail(SBIM_ERR_ARG, "side must be +1 or -1");
+  if (precision < SBIM_FP64 || precision > SBIM_BF16) return fail(SBIM_ERR_ARG, "bad precision");
+  sbim_ctx* c = new sbim_ctx;
+  c->n1 = n1; c->n3 = n3; c->L1 = L1; c->L3 = L3; c->cs = cs; c->cp = cp; c->rho = rho;
+  c->dt = dt; c->n_cut = n_cut; c->side = side; c->prec = precision;
+  c->kahan = precision == SBIM_FP64 ? 0 : (kahan ? 1 : 0);
+  c->stream = (cudaStream_t)stream;
+  const int rc = create_impl(c);
+  if (rc != SBIM_OK) {
+    const std::string msg = g_err;
+    release(c);
+    cudaGetLastError();
+    g_err = msg;
+    return rc;
+  }
+  *out = c;
+  return SBIM_OK;
+}
+
+int sbim_step(sbim_handle h, const void* u, const void* v, void* tau) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
+  sbim_ctx* c = h;
+  cudaStream_t st = c->stream;
+  cudaEvent_t* e = nullptr;
+  if (c->prof) {
+    if (c->prof_issued - c->prof_harvested >= kProfRing) {
+      const int rc = harvest(c, c->prof_issued - kProfRing + 1);
+      if (rc != SBIM_OK) return rc;
+    }
+    e = &c->ev[(c->prof_issued % kProfRing) * kProfEvents];
+    CU(cudaEventRecord(e[0], st));
+  }
+  if (c->prec == SBIM_FP64)
+    CF(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)u, (cufftDoubleComplex*)c->d_uhat));
+  else
+    CF(cufftExecR2C(c->plan_fwd, (cufftReal*)u, (cufftComplex*)c->d_uhat));
+  if (e) CU(cudaEventRecord(e[1], st));
+  const sbim::StepArgs a = step_args(c);
+  CU(sbim::launch_conv(a, c->prec, c->kahan, st));
+  if (e) CU(cudaEventRecord(e[2], st));
+  CU(sbim::launch_assemble(a, c->prec, c->kahan, st));
+  if (e) CU(cudaEventRecord(e[3], st));
+  if (c->prec == SBIM_FP64)
+    CF(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)c->d_s));
+  else
+    CF(cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)c->d_s));
+  if (e) CU(cudaEventRecord(e[4], st));
+  const double k = c->side * c->mu / c->cs;
+  const double coef[3] = {k, k * c->eta, k};
+  CU(sbim::launch_epilogue(c->prec, c->d_s, v, tau, (long long)c->n1 * c->n3, coef, c->tau_inf,
+                           c->d_step, st));
+  if (e) {
+    CU(cudaEventRecord(e[5], st));
+    ++c->prof_issued;
+  }
+  ++c->n;
+  return SBIM_OK;
+}
+
+int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
+  sbim_ctx* c = h;
+  const size_t bytes = c->field_elems() * c->real_size;
+  if (!c->d_io) CU(cudaMalloc(&c->d_io, 3 * bytes));
+  char* du = (char*)c->d_io;
+  char* dv = du + bytes;
+  char* dtau = dv + bytes;
+  CU(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, c->stream));
+  const int rc = sbim_step(h, du, dv, dtau);
+  if (rc != SBIM_OK) return rc;
+  CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SBIM_OK;
+}
+
+int sbim_set_far_field(sbim_handle h, const double tau_inf[3]) {
+  if (!h || !tau_inf) return fail(SBIM_ERR_ARG, "NULL argument");
+  for (int i = 0; i < 3; ++i) h->tau_inf[i] = tau_inf[i];
+  return SBIM_OK;
+}
+
+int sbim_reset(sbim_handle h) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  CU(cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream));
+  h->n = 0;
+  return SBIM_OK;
+}
+
+int sbim_get_step(sbim_handle h, long long* n) {
+  if (!h || !n) return fail(SBIM_ERR_ARG, "NULL argument");
+  *n = h->n;
+  return SBIM_OK;
+}
+
+int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots, long long* hist_bytes,
+                  long long* table_nodes) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (n_modes) *n_modes = h->nbins;
+  if (n_slots) *n_slots = (long long)h->n_orb_pad * 4;
+  if (hist_bytes) *hist_bytes = (long long)h->hist_bytes;
+  if (table_nodes) *table_nodes = h->tab_n;
+  return SBIM_OK;
+}
+
+int sbim_set_profiling(sbim_handle h, int enable) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (enable && h->ev.empty()) {
+    h->ev.resize((size_t)kProfRing * kProfEvents);
+    for (auto& e : h->ev) CU(cudaEventCreate(&e));
+  }
+  if (h->prof) {
+    const int rc = harvest(h, h->prof_issued);
+    if (rc != SBIM_OK) return rc;
+  }
+  h->prof = enable != 0;
+  h->prof_issued = h->prof_harvested = 0;
+  for (double& x : h->prof_ms) x = 0.0;
+  return SBIM_OK;
+}
+
+int sbim_stage_times(sbim_handle h, double ms[5], long long* steps) {
+  if (!h || !ms) return fail(SBIM_ERR_ARG, "NULL argument");
+  const int rc = harvest(h, h->prof_issued);
+  if (rc != SBIM_OK) return rc;
+  for (int k = 0; k < 5; ++k) ms[k] = h->prof_ms[k];
+  if (steps) *steps = h->prof_harvested;
+  return SBIM_OK;
+}
+
+int sbim_destroy(sbim_handle h) {
+  if (!h) return SBIM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  release(h);
+  return SBIM_OK;
+}
+
+const char* sbim_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal declarations shared by the translation units of libsbim.
+//
+// Spectral layout used by every kernel (Section 2.3, spectral evaluation of s_i):
+//   * Half spectra from the R2C transform: [3][n3][n1/2+1] complex, bin b =
+//     r3 * (n1/2+1) + j1.
+//   * "Orbits": the library groups the Fourier bins by |k| (all bins of one
+//     orbit share |k|, hence the kernel arguments T = m |k| c_s dt and the
+//     convolution weights), four "members" per orbit.  A member is one bin seen
+//     along one in-plane direction e = k/|k|; a bin on a Nyquist line appears as
+//     two (or, at the corner, four) members whose directions differ in the sign
+//     of the aliased component, each weighted 1/2 (1/4), which keeps only the
+//     part of the operator even in that component.  Orbits are sorted by |k|.
+//   * History ring buffer: [n_cut][3][n_orb_pad][4] complex (slot, component
+//     xi / 2 / perp, orbit, member); slot = step mod n_cut.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sbim {
+
+constexpr int kMembers = 4;      // members per orbit
+constexpr int kFields = 10;      // real accumulators per member: 5 complex sums
+constexpr int kOrbitTile = 128;  // orbits per CTA of the convolution kernel
+
+// Everything the per-step kernels read; device pointers unless noted.
+struct StepArgs {
+  // plan (read-only)
+  const int* bin;                  // [n_orb_pad*4] bin index, -1 = padding
+  const void* dir;                 // [n_orb_pad*4] (e1, e3) of the member (float2 / double2)
+  const float* wout;               // [n_orb_pad*4] output weight of the member
+  const void* dT;                  // [n_orb_pad] |k| c_s dt (float or double)
+  const unsigned long long* ustep; // [n_orb_pad] dT / h in 32.32 fixed point
+  const void* muq;                 // [n_orb_pad] mu |k| (float or double)
+  const void* table;               // [table_n] (H11, H22, H33, H12) at T = (j-1) h
+  // state
+  void* hist;                      // ring buffer (layout per precision)
+  long long* step;                 // device step counter n
+  void* part;                      // [nchunks][40][n_orb_pad] partial sums
+  const void* uhat;                // [3][nbins] forward spectra
+  void* fhat;                      // [3][nbins] output spectra (scaled 1/(n1 n3))
+  // sizes (host values)
+  int n_orb_pad;
+  int nbins;
+  int n_cut;
+  int lc;                          // lags per chunk
+  int nchunks;
+  int side;
+  double eta;
+  double inv_n;                    // 1 / (n1 n3)
+  long long slot_stride;           // elements of one history plane (BF16X2 lo offset)
+};
+
+cudaError_t launch_conv(const StepArgs& a, int precision, int kahan, cudaStream_t s);
+cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
+cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
+                            long long plane, const double coef[3], const double tau_inf[3],
+                            long long* step, cudaStream_t st);
+
+// FP64 quadrature of the half-space kernels on T_j = j h, j = -1 .. n-2.
+// out64 [n][4] doubles; out32 (optional) [n][4] floats.
+cudaError_t launch_table_build(double* out64, float* out32, long long n, double h,
+                               double eta, const double* gl_x, const double* gl_w,
+                               cudaStream_t s);
+
+}  // namespace sbim

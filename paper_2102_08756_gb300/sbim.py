@@ -1,0 +1,200 @@
+"""Thin Python binding of the C ABI in include/sbim.h (argument marshalling only).
+
+Every entry point of the library has a function of the same name here; they
+take plain integers / pointers and raise ``SBIMError`` on a non-zero status.
+``SBIM`` wraps a handle for torch CUDA tensors: the tensors supply device
+memory and the handle is bound to the current torch stream at creation.  Every
+step of the traction update runs in the library's kernels; there is no
+fallback when the library is missing -- loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libsbim.so")
+
+SBIM_OK = 0
+PRECISION = {"fp64": 0, "fp32": 1, "bf16x2": 2, "bf16": 3}
+STAGES = ("fft_forward", "convolution", "assemble", "fft_inverse", "epilogue")
+
+_lib = None
+
+
+class SBIMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sbim status {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libsbim.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    L.sbim_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, i, i, i, i, vp]
+    L.sbim_step.argtypes = [vp, vp, vp, vp]
+    L.sbim_step_host.argtypes = [vp, vp, vp, vp]
+    L.sbim_set_far_field.argtypes = [vp, ctypes.POINTER(d)]
+    L.sbim_reset.argtypes = [vp]
+    L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
+    L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
+    L.sbim_set_profiling.argtypes = [vp, i]
+    L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
+    L.sbim_destroy.argtypes = [vp]
+    L.sbim_last_error.argtypes = []
+    L.sbim_last_error.restype = ctypes.c_char_p
+    for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_set_far_field",
+                 "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
+                 "sbim_stage_times", "sbim_destroy"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != SBIM_OK:
+        raise SBIMError(code, lib().sbim_last_error().decode())
+
+
+# --- one function per C entry point ------------------------------------------
+def sbim_create(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, precision, kahan, stream):
+    h = ctypes.c_void_p()
+    _check(lib().sbim_create(ctypes.byref(h), n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side,
+                             precision, kahan, stream))
+    return h
+
+
+def sbim_step(h, u_ptr, v_ptr, tau_ptr):
+    _check(lib().sbim_step(h, u_ptr, v_ptr, tau_ptr))
+
+
+def sbim_step_host(h, u_ptr, v_ptr, tau_ptr):
+    _check(lib().sbim_step_host(h, u_ptr, v_ptr, tau_ptr))
+
+
+def sbim_set_far_field(h, tau_inf):
+    arr = (ctypes.c_double * 3)(*tau_inf)
+    _check(lib().sbim_set_far_field(h, arr))
+
+
+def sbim_reset(h):
+    _check(lib().sbim_reset(h))
+
+
+def sbim_get_step(h):
+    n = ctypes.c_longlong()
+    _check(lib().sbim_get_step(h, ctypes.byref(n)))
+    return n.value
+
+
+def sbim_get_info(h):
+    vals = [ctypes.c_longlong() for _ in range(4)]
+    _check(lib().sbim_get_info(h, *[ctypes.byref(v) for v in vals]))
+    return dict(zip(("n_modes", "n_slots", "hist_bytes", "table_nodes"), (v.value for v in vals)))
+
+
+def sbim_set_profiling(h, enable):
+    _check(lib().sbim_set_profiling(h, int(enable)))
+
+
+def sbim_stage_times(h):
+    ms = (ctypes.c_double * 5)()
+    n = ctypes.c_longlong()
+    _check(lib().sbim_stage_times(h, ms, ctypes.byref(n)))
+    return dict(zip(STAGES, list(ms))), n.value
+
+
+def sbim_destroy(h):
+    _check(lib().sbim_destroy(h))
+
+
+def sbim_last_error():
+    return lib().sbim_last_error().decode()
+
+
+# --- torch-facing wrapper ------------------------------------------------------
+class SBIM:
+    """One half-space boundary (Section 2.3, Eq. (SBI)) on an n1 x n3 periodic grid.
+
+    ``step(u, v)`` takes CUDA tensors [3, n3, n1] (float64 for precision
+    "fp64", float32 otherwise) and returns the traction tensor.
+    """
+
+    def __init__(self, n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, precision="fp32",
+                 kahan=True, stream=None):
+        import torch
+        self.torch = torch
+        self.n1, self.n3, self.n_cut, self.side = n1, n3, n_cut, side
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.device = stream.device
+        self.h = sbim_create(n1, n3, float(L1), float(L3), float(cs), float(cp), float(rho),
+                             float(dt), int(n_cut), int(side), PRECISION[precision],
+                             int(bool(kahan)), stream.cuda_stream)
+
+    def _field(self, x, name):
+        t = self.torch
+        if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == self.dtype
+                and tuple(x.shape) == (3, self.n3, self.n1) and x.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor "
+                             f"of shape (3, {self.n3}, {self.n1})")
+        return x.data_ptr()
+
+    def step(self, u, v, tau=None):
+        if tau is None:
+            tau = self.torch.empty_like(u)
+        sbim_step(self.h, self._field(u, "u"), self._field(v, "v"), self._field(tau, "tau"))
+        return tau
+
+    def step_host(self, u, v, tau=None):
+        """Host numpy arrays in and out (copies inside the call)."""
+        import numpy as np
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        u = np.ascontiguousarray(u, dtype=dt)
+        v = np.ascontiguousarray(v, dtype=dt)
+        if tau is None:
+            tau = np.empty_like(u)
+        for a in (u, v, tau):
+            if a.shape != (3, self.n3, self.n1) or a.dtype != dt or not a.flags.c_contiguous:
+                raise ValueError("host arrays must be C-contiguous (3, n3, n1)")
+        sbim_step_host(self.h, u.ctypes.data, v.ctypes.data, tau.ctypes.data)
+        return tau
+
+    def set_far_field(self, tau_inf):
+        sbim_set_far_field(self.h, tau_inf)
+
+    def reset(self):
+        sbim_reset(self.h)
+
+    @property
+    def n(self):
+        return sbim_get_step(self.h)
+
+    def info(self):
+        return sbim_get_info(self.h)
+
+    def set_profiling(self, enable=True):
+        sbim_set_profiling(self.h, enable)
+
+    def stage_times(self):
+        return sbim_stage_times(self.h)
+
+    def close(self):
+        if self.h is not None:
+            sbim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -97,7 +97,11 @@ def separable_history(n1, n3, L1, L3, steps, dt, cs, seed, *, n_terms=4,
                 keep[rng.choice(n3 * nh, size=min(sparse, n3 * nh), replace=False)] = True
                 spec = spec * keep.reshape(n3, nh)
             field = np.fft.irfft2(spec, s=(n3, n1))
-            Uh[r, c] = np.fft.rfft2(field)          # the spectrum the field really has
+            sp = np.fft.rfft2(field)                # the spectrum the field really has
+            if sparse is not None:                  # drop FFT round-off outside the bins
+                sp[np.abs(sp) < 1e-9 * np.abs(sp).max()] = 0.0
+                field = np.fft.irfft2(sp, s=(n3, n1))
+            Uh[r, c] = sp
             U[r, c] = field
     rms = np.sqrt(np.mean(U ** 2)) * np.sqrt(n_terms)
     if rms > 0:

@@ -1,0 +1,193 @@
+"""GPU parity of the SBIM traction update (Section 2.3, Eq. (SBI)) against the
+FP64 CPU oracle, through the C ABI.
+
+Metric: relative L2 error over the boundary field, per component, maximum over
+steps, on the non-local term s_i (runs with v = 0, so tau = s) and on the full
+traction tau_i.  Bounds: 1e-5 for float32 history (with or without
+compensated summation), 1e-9 for float64, 1e-4 for bf16 hi/lo and 1e-2 for
+bf16 hi-only history (the storage rounding of 2^-17 and 2^-9 per value).
+"""
+import numpy as np
+import pytest
+
+from oracle.sbim_oracle import (KernelTable, Material, ModeSet, SBIMOracle,
+                                apply_modal_operator, trapezoid_weights)
+from paper_2102_08756_gb300.synth import config_large, config_small, separable_history
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CS, CP, RHO = 3464.0, 6000.0, 2670.0
+TOL = {"fp64": 1e-9, "fp32": 1e-5, "bf16x2": 1e-4, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_l2(got, ref):
+    return max(np.linalg.norm(got[c] - ref[c]) / max(np.linalg.norm(ref[c]), 1e-300)
+               for c in range(3))
+
+
+def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
+               spectrum="band", dt=None, tau_inf=None):
+    from paper_2102_08756_gb300.sbim import SBIM
+    dt = dt or 0.3 * (L1 / n1) / CP
+    hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=seed, spectrum=spectrum)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    ndt = np.float64 if precision == "fp64" else np.float32
+    g_tau = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
+    g_s = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
+    o_tau = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side,
+                       tau_inf=tau_inf if tau_inf is not None else (0, 0, 0))
+    o_s = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
+    if tau_inf is not None:
+        g_tau.set_far_field(tau_inf)
+    err_s = err_t = 0.0
+    zero = torch.zeros((3, n3, n1), dtype=tdt, device="cuda")
+    for m in range(steps):
+        u = hist.u(m).astype(ndt)
+        v = hist.v(m).astype(ndt)
+        ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+        t = g_tau.step(ud, vd).double().cpu().numpy()
+        s = g_s.step(ud, zero).double().cpu().numpy()
+        rt = o_tau.step(u.astype(np.float64), v.astype(np.float64))
+        rs = o_s.step(u.astype(np.float64), np.zeros((3, n3, n1)))
+        if np.linalg.norm(rs["s"]) > 0:
+            err_s = max(err_s, rel_l2(s, rs["s"]))
+            err_t = max(err_t, rel_l2(t, rt["tau"]))
+    assert g_tau.n == steps
+    g_tau.close()
+    g_s.close()
+    return err_s, err_t
+
+
+@pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1), ("fp32", 0),
+                                             ("bf16x2", 1), ("bf16", 0)])
+@pytest.mark.parametrize("grid", [(4, 4, 400.0, 400.0), (16, 16, 1600.0, 1600.0),
+                                  (8, 6, 800.0, 900.0)])
+@pytest.mark.parametrize("n_cut,side", [(1, 1), (5, -1), (32, 1)])
+def test_tiny_grids_brute_force(precision, kahan, grid, n_cut, side):
+    """Every mode, every lag, ring-buffer wrap-around (steps > n_cut), Nyquist
+    lines of white-spectrum input, square and rectangular grids."""
+    n1, n3, L1, L3 = grid
+    steps = n_cut + 9
+    es, et = run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan,
+                        seed=n1 + n_cut, spectrum="k2")
+    assert es < TOL[precision], es
+    assert et < TOL[precision], et
+
+
+@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0)])
+def test_small_configuration(precision, kahan):
+    """64 x 64 boundary, dx = 100 m, 256-lag cutoff, 200 steps of band-limited
+    input: the small FP64 comparison case, every mode checked."""
+    c = config_small()
+    es, et = run_parity(c["n1"], c["n3"], c["L1"], c["L3"], c["n_cut"], 1, c["steps"],
+                        precision, kahan, seed=1001, dt=c["dt"])
+    assert es < TOL[precision], es
+    assert et < TOL[precision], et
+
+
+def test_far_field_and_uniform_mode():
+    es, et = run_parity(8, 8, 800.0, 800.0, 6, -1, 10, "fp32", 1, seed=3,
+                        tau_inf=(1.5e6, -7.0e7, 3.0e5))
+    assert et < 1e-5
+
+
+def test_step_host_matches_device_step():
+    from paper_2102_08756_gb300.sbim import SBIM
+    n, dx = 32, 100.0
+    dt = 0.3 * dx / CP
+    hist = separable_history(n, n, n * dx, n * dx, 12, dt, CS, seed=9)
+    a = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
+    b = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
+    for m in range(12):
+        u = hist.u(m).astype(np.float32)
+        v = hist.v(m).astype(np.float32)
+        t_dev = a.step(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
+        t_host = b.step_host(u, v)
+        np.testing.assert_array_equal(t_dev, t_host)
+
+
+def test_reset_restarts_history():
+    from paper_2102_08756_gb300.sbim import SBIM
+    n, dx = 16, 100.0
+    dt = 0.3 * dx / CP
+    hist = separable_history(n, n, n * dx, n * dx, 7, dt, CS, seed=2)
+    g = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 16, 1, "fp32", True)
+    outs = []
+    for rep in range(2):
+        g.reset()
+        assert g.n == 0
+        outs.append([g.step(torch.from_numpy(hist.u(m).astype(np.float32)).cuda(),
+                            torch.from_numpy(hist.v(m).astype(np.float32)).cuda()).cpu().numpy()
+                     for m in range(7)])
+    for x, y in zip(*outs):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_profiling_stage_times():
+    from paper_2102_08756_gb300.sbim import SBIM
+    n = 64
+    g = SBIM(n, n, 6400.0, 6400.0, CS, CP, RHO, 0.005, 64, 1, "fp32", True)
+    g.set_profiling(True)
+    u = torch.zeros((3, n, n), device="cuda")
+    for _ in range(5):
+        g.step(u, u)
+    times, steps = g.stage_times()
+    assert steps == 5 and all(t >= 0 for t in times.values())
+    assert times["convolution"] > 0
+
+
+@pytest.mark.parametrize("precision,kahan,tol", [("fp32", 1, 1e-5), ("bf16x2", 1, 1e-4)])
+def test_large_boundary_sampled_modes(precision, kahan, tol):
+    """1024 x 1024 boundary with the full 4096-lag history (plus wrap-around),
+    in the launch configuration the benchmark times.  Input: two separable
+    terms on 2 x 600 random Fourier bins with exactly known spectra; the last
+    step's non-local traction spectrum (FP64 FFT of the GPU output) is compared
+    bin by bin on those bins with the oracle's per-mode operator."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    c = config_large()
+    n1, n3, L1, L3, n_cut, dt = c["n1"], c["n3"], c["L1"], c["L3"], c["n_cut"], c["dt"]
+    steps = n_cut + 37
+    side = -1
+    hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=3003, n_terms=2,
+                             spectrum="k2", sparse=600)
+    g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
+    U = torch.from_numpy(hist.U.astype(np.float32)).cuda()
+    gT = torch.from_numpy(hist.g.astype(np.float32))
+    zero = torch.zeros((3, n3, n1), device="cuda")
+    u = torch.empty((3, n3, n1), device="cuda")
+    tau = torch.empty_like(u)
+    for m in range(steps):
+        torch.mul(U[0], float(gT[0, m]), out=u)
+        u.add_(U[1], alpha=float(gT[1, m]))
+        g.step(u, zero, tau)
+    torch.cuda.synchronize()
+    F_gpu = np.fft.rfft2(tau.double().cpu().numpy())
+    g.close()
+
+    nz = np.nonzero(np.abs(hist.Uhat).sum(axis=(0, 1)) > 0)
+    r3, j1 = nz[0], nz[1]
+    modes = ModeSet.build(n1, n3, L1, L3, r3=r3, j1=j1)
+    mat = Material(CS, CP, RHO)
+    dT = modes.q * CS * dt
+    kt = KernelTable(mat.eta, float(dT.max()) * n_cut + 1)
+    uniq, inv = np.unique(dT, return_inverse=True)
+    wu = np.stack([trapezoid_weights(d, n_cut, kt) for d in uniq], axis=1)
+    w = wu[:, inv, :]
+    nlast = steps - 1
+    lags = np.arange(n_cut)
+    gl = hist.g[:, nlast - lags]                                   # (R, L)
+    Uh = hist.Uhat[:, :, r3, j1]                                   # (R, 3, nsel)
+    hist_rev = np.einsum("rl,rcq->lcq", gl, Uh)
+    F_ref = apply_modal_operator(modes, mat, side, w, hist_rev, hist_rev[0])
+    got = F_gpu[:, r3, j1]
+    err = max(np.linalg.norm(got[k] - F_ref[k]) / np.linalg.norm(F_ref[k]) for k in range(3))
+    assert err < tol, err
