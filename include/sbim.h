@@ -141,6 +141,41 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
 int sbim_set_profiling(sbim_handle h, int enable);
 int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
 
+/*
+ * sbim_spectral_response_noalloc -- the non-local traction spectrum of one
+ * half-space for a caller-supplied displacement-spectrum history, without
+ * allocating any device memory.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory -- a solver handed its
+ * device buffers by a host framework that owns a fixed memory arena, or a
+ * plugin whose device footprint must stay constant while the host time-steps --
+ * and therefore cannot use sbim_create, which allocates the history ring
+ * buffer, the kernel tables and the FFT plans.
+ *
+ *   n1, n3, L1, L3, cs, cp, rho, dt, side   as for sbim_create
+ *   n_lags     number of history steps to convolve (>= 1); lag 0 is the current step
+ *   uhat_hist  device pointer, complex float (re, im) [n_lags][3][n3][n1/2+1]: the
+ *              unnormalised forward R2C spectra of the three Cartesian displacement
+ *              components at steps n, n-1, ..., n-n_lags+1 (lag-major)
+ *   fhat       device pointer, complex float [3][n3][n1/2+1], output: the
+ *              unnormalised forward spectrum of s_i at step n (s_i is its inverse
+ *              R2C transform scaled by 1/(n1 n3))
+ *   stream     cudaStream_t the kernels run on (NULL = legacy default stream)
+ * Float32 history, compensated accumulation; same kernels, quadrature and Nyquist
+ * treatment as sbim_step.  Working memory is one static device array of 64 MiB
+ * that every GPU which loads the library keeps until the process exits; it holds
+ * the kernel table and the lag-chunk partial sums.  Limits (SBIM_ERR_ARG
+ * otherwise): n3 (n1/2+1) <= 655,296 bins, and |k|max c_s dt (n_lags - 1) <= 8191.9.
+ * The first call on a device (and any call with a new cp/cs or a longer history
+ * range) resolves the array's device address and builds the kernel table, waiting
+ * for the stream; make that first call before any stream capture.  All calls
+ * share the array and keep the last call's contents: calls whose kernels overlap
+ * on the GPU (other streams or host threads) race and must be serialised by the
+ * caller.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int sbim_spectral_response_noalloc(int n1, int n3, double L1, double L3, double cs,
+                                   double cp, double rho, double dt, int side, int n_lags,
+                                   const void* uhat_hist, void* fhat, void* stream);
+
 /* sbim_destroy -- free everything the handle owns; NULL is accepted. */
 int sbim_destroy(sbim_handle h);
 

@@ -419,6 +419,10 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
 
 }  // namespace
 
+namespace sbim {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace sbim
+
 extern "C" {
 
 int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double cs, double cp,

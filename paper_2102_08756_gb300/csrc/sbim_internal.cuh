@@ -63,4 +63,7 @@ cudaError_t launch_table_build(double* out64, float* out32, long long n, double 
                                double eta, const double* gl_x, const double* gl_w,
                                cudaStream_t s);
 
+// Set the calling thread's message returned by sbim_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace sbim

@@ -46,12 +46,13 @@ def lib():
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
     L.sbim_set_profiling.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
+    L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
     L.sbim_last_error.argtypes = []
     L.sbim_last_error.restype = ctypes.c_char_p
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
-                 "sbim_stage_times", "sbim_destroy"):
+                 "sbim_stage_times", "sbim_spectral_response_noalloc", "sbim_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -108,6 +109,14 @@ def sbim_stage_times(h):
     n = ctypes.c_longlong()
     _check(lib().sbim_stage_times(h, ms, ctypes.byref(n)))
     return dict(zip(STAGES, list(ms))), n.value
+
+
+def sbim_spectral_response_noalloc(n1, n3, L1, L3, cs, cp, rho, dt, side, n_lags, uhat_ptr,
+                                   fhat_ptr, stream):
+    """Allocation-free non-local traction spectrum for callers that may not
+    allocate device memory (see include/sbim.h); device pointers in and out."""
+    _check(lib().sbim_spectral_response_noalloc(n1, n3, L1, L3, cs, cp, rho, dt, side, n_lags,
+                                                uhat_ptr, fhat_ptr, stream))
 
 
 def sbim_destroy(h):
