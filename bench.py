@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x2", "bf16"])
     p.add_argument("--kahan", type=int, default=1)
+    p.add_argument("--variant", type=int, default=1, help="convolution kernel: 1 TMA-staged, 0 register prefetch")
+    p.add_argument("--lags-per-cta", type=int, default=0)
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,6 +242,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     g = SBIM(n1, n3, c["L1"], c["L3"], c["cs"], c["cp"], c["rho"], dt, n_cut, 1, prec,
              bool(args.kahan), stream=stream)
+    g.set_conv_config(args.variant, args.lags_per_cta)
     K, W = args.steps, args.warmup
     total_steps = n_cut + W + K
     hist = separable_history(n1, n3, c["L1"], c["L3"], total_steps + 1, dt, c["cs"],
@@ -293,6 +296,7 @@ def run_native(args):
     ms_total = e0.elapsed_time(e1)
     stage, nprof = g.stage_times()
     g.set_profiling(False)
+    g.check()
     hist_bytes = g.info()["hist_bytes"]
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
@@ -362,6 +366,7 @@ def run_native(args):
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(c, prec, args.kahan), "n1": n1, "n3": n3,
                    "n_cut": n_cut, "precision": prec, "kahan": int(bool(args.kahan)),
+                   "conv_variant": "tma" if args.variant == 1 else "ldg",
                    "modes": modes, "history_bytes": hist_bytes,
                    "l2": "inputs larger than L2 (history ring buffer >> 129 MB)",
                    "parallelism": f"replicas x{world}"},

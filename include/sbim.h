@@ -107,6 +107,24 @@ int sbim_step(sbim_handle h, const void* u, const void* v, void* tau);
 int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau);
 
 /*
+ * sbim_step_adjoint -- transpose of one sbim_step, for reverse-time (adjoint)
+ * sweeps that differentiate a function of the tractions (Section 2.3, Eq. (SBI);
+ * the transpose of the convolution is the time-reversed correlation with the same
+ * kernels).  For a sequence of N forward steps from rest, tau_n(u_0..u_n, v_n),
+ * and a cotangent tau_bar_n = dJ/dtau_n, calling this N times with
+ * tau_bar_{N-1}, ..., tau_bar_0 on a fresh (or just reset) handle with the same
+ * parameters returns, call by call, u_bar_m = dJ/du_m and v_bar_m = dJ/dv_m for
+ * m = N-1, ..., 0, with sum_n <tau_n, tau_bar_n> = sum_m <u_m, u_bar_m> + <v_m, v_bar_m>
+ * (far-field term excluded).  The handle's history then holds tau_bar spectra:
+ * do not interleave forward and adjoint calls without sbim_reset.
+ *   tau_bar  device pointer, input  [3][n3][n1]
+ *   u_bar    device pointer, output [3][n3][n1]
+ *   v_bar    device pointer, output [3][n3][n1] (= -side (mu/c_s) eta tau_bar)
+ * The three buffers must be distinct.  Stream-ordered like sbim_step.
+ */
+int sbim_step_adjoint(sbim_handle h, const void* tau_bar, void* u_bar, void* v_bar);
+
+/*
  * sbim_set_far_field -- tau_i^inf of Eq. (SBI) (Pa), a uniform far-field
  * traction added to every output; default (0, 0, 0).
  */
@@ -140,6 +158,27 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
  */
 int sbim_set_profiling(sbim_handle h, int enable);
 int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
+
+/*
+ * sbim_set_conv_config -- launch configuration of the history convolution
+ * (Section 2.3, the per-mode time convolution), the knob a tuner turns.
+ *   variant       1 (default): history slots staged in shared memory by TMA bulk
+ *                 copies, blocked compensated sums; 0: per-thread register
+ *                 prefetch, per-term compensated sums
+ *   lags_per_cta  lags one CTA convolves (0 = automatic: ~16 waves of resident CTAs)
+ * Both variants compute the same sums to within float rounding.  May reallocate
+ * the lag-chunk partial buffer (synchronising the stream); on failure the
+ * previous configuration is kept.
+ */
+int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta);
+
+/*
+ * sbim_check_device -- wait for the handle's stream and report whether any
+ * bounded device-side wait of the convolution gave up since the last check
+ * (SBIM_ERR_TIMEOUT; the tractions computed since then are invalid).  Clears the
+ * flag.  sbim_step_host performs this check after every step.
+ */
+int sbim_check_device(sbim_handle h);
 
 /*
  * sbim_spectral_response_noalloc -- the non-local traction spectrum of one

@@ -445,3 +445,97 @@ class SBIMOracle:
                - coef * self.mat.impedance[:, None, None] * v + s)
         self.n += 1
         return {"tau": tau, "s": s, "F": F, "imag": imag}
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (transpose) of a sequence of traction updates, built as the literal
+# transpose of each stage of the forward map for the real inner products
+# <a, b> = sum_x a(x) b(x) on fields and sum over (Re, Im) parts on half spectra.
+# ---------------------------------------------------------------------------
+def modal_matrices(modes, mat, side, weights):
+    """Cartesian 3x3 modal matrices A(m) with F_n = sum_m A(m) Uhat_{n-m}
+    (Section 2.3; the same operator as ``apply_modal_operator``, written out
+    entry by entry).  weights: (4, nmodes, L); returns (L, nmodes, 3, 3)."""
+    mu, eta = mat.mu, mat.eta
+    q = modes.q
+    qs = np.where(q > 0, q, 1.0)
+    e1, e3 = modes.k1 / qs, modes.k3 / qs
+    odd = modes.nyq1 | modes.nyq3
+    e11, e33 = e1 * e1, e3 * e3
+    e13 = np.where(odd, 0.0, e1 * e3)
+    c1 = np.where(modes.nyq1, 0.0, e1)
+    c3 = np.where(modes.nyq3, 0.0, e3)
+    L = weights.shape[2]
+    A = np.zeros((L, len(modes), 3, 3), dtype=complex)
+    for m in range(L):
+        w11, w22, w33, w12 = (weights[k][:, m] for k in range(4))
+        cpl = w12 + ((2.0 - eta) if m == 0 else 0.0)
+        d = -side * mu * q
+        A[m, :, 0, 0] = d * (e11 * w11 + e33 * w33)
+        A[m, :, 0, 2] = d * (e13 * w11 - e13 * w33)
+        A[m, :, 2, 0] = d * (e13 * w11 - e13 * w33)
+        A[m, :, 2, 2] = d * (e33 * w11 + e11 * w33)
+        A[m, :, 1, 1] = d * w22
+        A[m, :, 0, 1] = 1j * mu * q * c1 * cpl
+        A[m, :, 2, 1] = 1j * mu * q * c3 * cpl
+        A[m, :, 1, 0] = -1j * mu * q * c1 * cpl
+        A[m, :, 1, 2] = -1j * mu * q * c3 * cpl
+    A[:, q == 0] = 0.0
+    return A
+
+
+def _half_column_weights(n1, n3):
+    """c_k of the real inner product of half spectra: 1 on the self-conjugate
+    columns j1 = 0 and j1 = n1/2, 2 elsewhere."""
+    c = np.full((n3, n1 // 2 + 1), 2.0)
+    c[:, 0] = 1.0
+    c[:, n1 // 2] = 1.0
+    return c
+
+
+def dft2_inverse_transpose(g):
+    """Transpose of ``dft2_inverse`` (half spectrum -> real field):
+    F_bar = (c_k / (n1 n3)) x forward DFT of g."""
+    g = np.asarray(g, dtype=float)
+    _, n3, n1 = g.shape
+    return dft2_forward(g) * (_half_column_weights(n1, n3) / (n1 * n3))[None]
+
+
+def dft2_forward_transpose(Ub, n1):
+    """Transpose of ``dft2_forward`` (real field -> half spectrum):
+    u_bar(x) = Re sum_{half k} Ub_k e^{+i k x} (no doubling, no 1/N)."""
+    Ub = np.asarray(Ub, dtype=complex)
+    nc, n3, nh = Ub.shape
+    E3 = _dft_matrix(n3, n3, +1.0)                     # [x3][r3]
+    E1 = _dft_matrix(n1, n1, +1.0)[:, :nh]             # [x1][j1]
+    return np.stack([(E3 @ Ub[c] @ E1.T).real for c in range(nc)])
+
+
+def adjoint_sequence(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, tau_bar, kernel="table"):
+    """Transpose of N consecutive updates started from rest: given tau_bar_n
+    (N, 3, n3, n1), returns (u_bar, v_bar) with
+    sum_n <tau_n, tau_bar_n> = sum_m <u_m, u_bar_m> + <v_m, v_bar_m>."""
+    tau_bar = np.asarray(tau_bar, dtype=float)
+    N = tau_bar.shape[0]
+    mat = Material(cs, cp, rho)
+    modes = ModeSet.build(n1, n3, L1, L3)
+    dT = modes.q * cs * dt
+    if kernel == "table":
+        kern = KernelTable(mat.eta, float(dT.max()) * max(n_cut - 1, 1) + 1.0)
+    else:
+        kern = lambda T: kernels_direct(T, mat.eta)  # noqa: E731
+    uniq, inv = np.unique(dT, return_inverse=True)
+    wu = np.stack([trapezoid_weights(d, n_cut, kern) for d in uniq], axis=1)
+    A = modal_matrices(modes, mat, side, wu[:, inv, :])           # (L, nm, 3, 3)
+    AH = np.conj(np.swapaxes(A, 2, 3))
+    nh = n1 // 2 + 1
+    G = [dft2_inverse_transpose(tb).reshape(3, -1) for tb in tau_bar]
+    u_bar = np.empty_like(tau_bar)
+    for m in range(N):
+        Ub = np.zeros((3, n3 * nh), dtype=complex)
+        for lag in range(min(n_cut, N - m)):
+            Ub += np.einsum("qab,bq->aq", AH[lag], G[m + lag])
+        u_bar[m] = dft2_forward_transpose(Ub.reshape(3, n3, nh), n1)
+    coef = side * mat.mu / cs
+    v_bar = -coef * mat.impedance[None, :, None, None] * tau_bar
+    return u_bar, v_bar

@@ -105,6 +105,9 @@ struct sbim_ctx {
   double L1 = 0, L3 = 0, cs = 0, cp = 0, rho = 0, dt = 0, mu = 0, eta = 0;
   cudaStream_t stream = nullptr;
   int n_orb = 0, n_orb_pad = 0, lc = 1, nchunks = 1;
+  int variant = 1;            // 0: register-prefetch loads, 1: TMA-staged history
+  int lags_per_cta = 0;       // 0: automatic
+  size_t part_bytes = 0;
   double tab_h = 0;
   long long tab_n = 0;
   size_t real_size = 4;
@@ -126,6 +129,7 @@ struct sbim_ctx {
   void* d_fhat = nullptr;
   void* d_s = nullptr;
   long long* d_step = nullptr;
+  int* d_err = nullptr;
   void* d_io = nullptr;  // u, v, tau staging for sbim_step_host
   cufftHandle plan_fwd = 0, plan_inv = 0;
   bool have_fwd = false, have_inv = false;
@@ -226,17 +230,41 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
   }
 }
 
+// Lag chunking of the convolution grid: (n_orb_pad / 128) x nchunks CTAs,
+// about 16 waves of the variant's resident CTAs, unless lags_per_cta is set.
 int choose_chunks(sbim_ctx& c) {
   int dev = 0, sms = 148;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const long long tiles = c.n_orb_pad / sbim::kOrbitTile;
-  const long long target = (long long)sms * 3 * 16;
-  long long S = (target + tiles - 1) / tiles;
-  const long long smax = std::max(1, (c.n_cut + 15) / 16);
-  S = std::max(1LL, std::min(S, smax));
-  c.lc = (int)((c.n_cut + S - 1) / S);
+  if (c.lags_per_cta > 0) {
+    c.lc = std::min(c.lags_per_cta, c.n_cut);
+  } else {
+    const long long tiles = c.n_orb_pad / sbim::kOrbitTile;
+    const int per_sm = c.variant == 1 ? sbim::conv_tma_ctas_per_sm(c.prec)
+                                      : (c.prec == SBIM_FP64 ? 1 : 3);
+    const long long target = (long long)sms * per_sm * 16;
+    long long S = (target + tiles - 1) / tiles;
+    const long long smax = std::max(1, (c.n_cut + 15) / 16);
+    S = std::max(1LL, std::min(S, smax));
+    c.lc = (int)((c.n_cut + S - 1) / S);
+  }
   c.nchunks = (c.n_cut + c.lc - 1) / c.lc;
+  return SBIM_OK;
+}
+
+// (Re)allocate the lag-chunk partial sums for the current chunking; on failure
+// the previous buffer is kept.
+int alloc_partials(sbim_ctx& c) {
+  const size_t need = (size_t)c.nchunks * 4 * sbim::kFields * c.n_orb_pad * c.real_size;
+  if (need <= c.part_bytes && c.d_part) return SBIM_OK;
+  void* fresh = nullptr;
+  CU(cudaMalloc(&fresh, need));
+  if (c.d_part) {
+    CU(cudaStreamSynchronize(c.stream));
+    CU(cudaFree(c.d_part));
+  }
+  c.d_part = fresh;
+  c.part_bytes = need;
   return SBIM_OK;
 }
 
@@ -246,7 +274,7 @@ void release(sbim_ctx* c) {
   if (c->have_inv) cufftDestroy(c->plan_inv);
   void* ptrs[] = {c->d_bin, c->d_dir, c->d_wout, c->d_dT, c->d_ustep, c->d_muq,
                   c->d_tab64, c->d_tab32, c->d_gl, c->d_hist, c->d_part, c->d_uhat,
-                  c->d_fhat, c->d_s, c->d_step, c->d_io};
+                  c->d_fhat, c->d_s, c->d_step, c->d_err, c->d_io};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -344,11 +372,13 @@ int create_impl(sbim_ctx* c) {
   if (!dbl) CU(cudaMalloc(&c->d_tab32, (size_t)c->tab_n * 4 * sizeof(float)));
   CU(cudaMalloc(&c->d_gl, 32 * sizeof(double)));
   CU(cudaMalloc(&c->d_hist, c->hist_bytes));
-  CU(cudaMalloc(&c->d_part, part_bytes));
+  c->d_part = nullptr;
+  if (alloc_partials(*c) != SBIM_OK) return SBIM_ERR_OOM;
   CU(cudaMalloc(&c->d_uhat, 3 * (size_t)c->nbins * cplx));
   CU(cudaMalloc(&c->d_fhat, 3 * (size_t)c->nbins * cplx));
   CU(cudaMalloc(&c->d_s, c->field_elems() * c->real_size));
   CU(cudaMalloc(&c->d_step, sizeof(long long)));
+  CU(cudaMalloc(&c->d_err, sizeof(int)));
 
   cudaStream_t st = c->stream;
   CU(cudaMemcpyAsync(c->d_bin, h_bin.data(), h_bin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -376,6 +406,7 @@ int create_impl(sbim_ctx* c) {
   CU(sbim::launch_table_build(c->d_tab64, c->d_tab32, c->tab_n, c->tab_h, c->eta, c->d_gl,
                               c->d_gl + 16, st));
   CU(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   CU(cudaStreamSynchronize(st));
 
   // cuFFT plans: batch of 3 components, [n3][n1] real <-> [n3][n1/2+1] complex
@@ -402,6 +433,7 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
   a.table = c->prec == SBIM_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
   a.hist = c->d_hist;
   a.step = c->d_step;
+  a.err = c->d_err;
   a.part = c->d_part;
   a.uhat = c->d_uhat;
   a.fhat = c->d_fhat;
@@ -456,10 +488,16 @@ int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double c
   return SBIM_OK;
 }
 
-int sbim_step(sbim_handle h, const void* u, const void* v, void* tau) {
-  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
-  if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
-  sbim_ctx* c = h;
+}  // extern "C"
+
+namespace {
+
+// One update: forward (in = u, aux = v, out = tau) or its transpose in reverse
+// time (in = tau_bar, out = u_bar, aux = v_bar).  The per-bin, per-lag modal
+// matrix is Hermitian in the (xi, 2, perp) frame ([a, ib; -ib, d] and a real
+// perp entry), so the transpose of R2C -> A -> C2R/N is the same map; applied to
+// the tau_bar sequence in reverse time it gives the time-reversed correlation.
+int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoint) {
   cudaStream_t st = c->stream;
   cudaEvent_t* e = nullptr;
   if (c->prof) {
@@ -471,30 +509,56 @@ int sbim_step(sbim_handle h, const void* u, const void* v, void* tau) {
     CU(cudaEventRecord(e[0], st));
   }
   if (c->prec == SBIM_FP64)
-    CF(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)u, (cufftDoubleComplex*)c->d_uhat));
+    CF(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)in, (cufftDoubleComplex*)c->d_uhat));
   else
-    CF(cufftExecR2C(c->plan_fwd, (cufftReal*)u, (cufftComplex*)c->d_uhat));
+    CF(cufftExecR2C(c->plan_fwd, (cufftReal*)in, (cufftComplex*)c->d_uhat));
   if (e) CU(cudaEventRecord(e[1], st));
   const sbim::StepArgs a = step_args(c);
-  CU(sbim::launch_conv(a, c->prec, c->kahan, st));
+  if (c->variant == 1)
+    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, st));
+  else
+    CU(sbim::launch_conv(a, c->prec, c->kahan, st));
   if (e) CU(cudaEventRecord(e[2], st));
   CU(sbim::launch_assemble(a, c->prec, c->kahan, st));
   if (e) CU(cudaEventRecord(e[3], st));
+  void* s_dst = adjoint ? out : c->d_s;
   if (c->prec == SBIM_FP64)
-    CF(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)c->d_s));
+    CF(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)s_dst));
   else
-    CF(cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)c->d_s));
+    CF(cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)s_dst));
   if (e) CU(cudaEventRecord(e[4], st));
   const double k = c->side * c->mu / c->cs;
   const double coef[3] = {k, k * c->eta, k};
-  CU(sbim::launch_epilogue(c->prec, c->d_s, v, tau, (long long)c->n1 * c->n3, coef, c->tau_inf,
-                           c->d_step, st));
+  const long long plane = (long long)c->n1 * c->n3;
+  if (adjoint)
+    CU(sbim::launch_adjoint_epilogue(c->prec, in, const_cast<void*>(aux), plane, coef,
+                                     c->d_step, st));
+  else
+    CU(sbim::launch_epilogue(c->prec, c->d_s, aux, out, plane, coef, c->tau_inf, c->d_step, st));
   if (e) {
     CU(cudaEventRecord(e[5], st));
     ++c->prof_issued;
   }
   ++c->n;
   return SBIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbim_step(sbim_handle h, const void* u, const void* v, void* tau) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
+  return run_step(h, u, v, tau, false);
+}
+
+int sbim_step_adjoint(sbim_handle h, const void* tau_bar, void* u_bar, void* v_bar) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!tau_bar || !u_bar || !v_bar) return fail(SBIM_ERR_ARG, "NULL field pointer");
+  if (tau_bar == u_bar || tau_bar == v_bar || u_bar == v_bar)
+    return fail(SBIM_ERR_ARG, "tau_bar, u_bar and v_bar must be distinct buffers");
+  return run_step(h, tau_bar, v_bar, u_bar, true);
 }
 
 int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
@@ -512,6 +576,35 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
   if (rc != SBIM_OK) return rc;
   CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  return sbim_check_device(h);
+}
+
+int sbim_check_device(sbim_handle h) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  int flag = 0;
+  CU(cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (flag) {
+    CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    return fail(SBIM_ERR_TIMEOUT, "a bounded device wait gave up; the outputs since the last check "
+                                  "are invalid");
+  }
+  return SBIM_OK;
+}
+
+int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (variant != 0 && variant != 1) return fail(SBIM_ERR_ARG, "variant must be 0 or 1");
+  if (lags_per_cta < 0) return fail(SBIM_ERR_ARG, "lags_per_cta must be >= 0");
+  const int old_v = h->variant, old_l = h->lags_per_cta, old_lc = h->lc, old_nc = h->nchunks;
+  h->variant = variant;
+  h->lags_per_cta = lags_per_cta;
+  int rc = choose_chunks(*h);
+  if (rc == SBIM_OK) rc = alloc_partials(*h);
+  if (rc != SBIM_OK) {
+    h->variant = old_v; h->lags_per_cta = old_l; h->lc = old_lc; h->nchunks = old_nc;
+    return rc;
+  }
   return SBIM_OK;
 }
 

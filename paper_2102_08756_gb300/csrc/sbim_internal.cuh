@@ -36,6 +36,7 @@ struct StepArgs {
   // state
   void* hist;                      // ring buffer (layout per precision)
   long long* step;                 // device step counter n
+  int* err;                        // device error word (bounded waits that gave up)
   void* part;                      // [nchunks][40][n_orb_pad] partial sums
   const void* uhat;                // [3][nbins] forward spectra
   void* fhat;                      // [3][nbins] output spectra (scaled 1/(n1 n3))
@@ -52,10 +53,19 @@ struct StepArgs {
 };
 
 cudaError_t launch_conv(const StepArgs& a, int precision, int kahan, cudaStream_t s);
+// History convolution with TMA bulk-copy staging of the history slots in shared
+// memory (same inputs and outputs as launch_conv).  ctas_per_sm reports the
+// residency the launch is sized for.
+cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, cudaStream_t s);
+int conv_tma_ctas_per_sm(int precision);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
                             long long plane, const double coef[3], const double tau_inf[3],
                             long long* step, cudaStream_t st);
+
+cudaError_t launch_adjoint_epilogue(int precision, const void* tau_bar, void* v_bar,
+                                    long long plane, const double coef[3], long long* step,
+                                    cudaStream_t st);
 
 // FP64 quadrature of the half-space kernels on T_j = j h, j = -1 .. n-2.
 // out64 [n][4] doubles; out32 (optional) [n][4] floats.

@@ -40,19 +40,24 @@ def lib():
     L.sbim_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, i, i, i, i, vp]
     L.sbim_step.argtypes = [vp, vp, vp, vp]
     L.sbim_step_host.argtypes = [vp, vp, vp, vp]
+    L.sbim_step_adjoint.argtypes = [vp, vp, vp, vp]
     L.sbim_set_far_field.argtypes = [vp, ctypes.POINTER(d)]
     L.sbim_reset.argtypes = [vp]
     L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
     L.sbim_set_profiling.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
+    L.sbim_set_conv_config.argtypes = [vp, i, i]
+    L.sbim_check_device.argtypes = [vp]
     L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
     L.sbim_last_error.argtypes = []
     L.sbim_last_error.restype = ctypes.c_char_p
-    for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_set_far_field",
+    for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
+                 "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
-                 "sbim_stage_times", "sbim_spectral_response_noalloc", "sbim_destroy"):
+                 "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device",
+                 "sbim_spectral_response_noalloc", "sbim_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -77,6 +82,10 @@ def sbim_step(h, u_ptr, v_ptr, tau_ptr):
 
 def sbim_step_host(h, u_ptr, v_ptr, tau_ptr):
     _check(lib().sbim_step_host(h, u_ptr, v_ptr, tau_ptr))
+
+
+def sbim_step_adjoint(h, tau_bar_ptr, u_bar_ptr, v_bar_ptr):
+    _check(lib().sbim_step_adjoint(h, tau_bar_ptr, u_bar_ptr, v_bar_ptr))
 
 
 def sbim_set_far_field(h, tau_inf):
@@ -109,6 +118,14 @@ def sbim_stage_times(h):
     n = ctypes.c_longlong()
     _check(lib().sbim_stage_times(h, ms, ctypes.byref(n)))
     return dict(zip(STAGES, list(ms))), n.value
+
+
+def sbim_set_conv_config(h, variant, lags_per_cta=0):
+    _check(lib().sbim_set_conv_config(h, int(variant), int(lags_per_cta)))
+
+
+def sbim_check_device(h):
+    _check(lib().sbim_check_device(h))
 
 
 def sbim_spectral_response_noalloc(n1, n3, L1, L3, cs, cp, rho, dt, side, n_lags, uhat_ptr,
@@ -164,6 +181,16 @@ class SBIM:
         sbim_step(self.h, self._field(u, "u"), self._field(v, "v"), self._field(tau, "tau"))
         return tau
 
+    def step_adjoint(self, tau_bar, u_bar=None, v_bar=None):
+        """Transpose of one step (reverse-time sweeps, see include/sbim.h)."""
+        if u_bar is None:
+            u_bar = self.torch.empty_like(tau_bar)
+        if v_bar is None:
+            v_bar = self.torch.empty_like(tau_bar)
+        sbim_step_adjoint(self.h, self._field(tau_bar, "tau_bar"), self._field(u_bar, "u_bar"),
+                          self._field(v_bar, "v_bar"))
+        return u_bar, v_bar
+
     def step_host(self, u, v, tau=None):
         """Host numpy arrays in and out (copies inside the call)."""
         import numpy as np
@@ -196,6 +223,13 @@ class SBIM:
 
     def stage_times(self):
         return sbim_stage_times(self.h)
+
+    def set_conv_config(self, variant, lags_per_cta=0):
+        sbim_set_conv_config(self.h, variant, lags_per_cta)
+
+    def check(self):
+        """Wait for the stream; raise if a bounded device wait gave up."""
+        sbim_check_device(self.h)
 
     def close(self):
         if self.h is not None:

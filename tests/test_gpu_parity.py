@@ -35,7 +35,7 @@ def rel_l2(got, ref):
 
 
 def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
-               spectrum="band", dt=None, tau_inf=None):
+               spectrum="band", dt=None, tau_inf=None, variant=1):
     from paper_2102_08756_gb300.sbim import SBIM
     dt = dt or 0.3 * (L1 / n1) / CP
     hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=seed, spectrum=spectrum)
@@ -46,6 +46,8 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
     o_tau = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side,
                        tau_inf=tau_inf if tau_inf is not None else (0, 0, 0))
     o_s = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
+    g_tau.set_conv_config(variant)
+    g_s.set_conv_config(variant)
     if tau_inf is not None:
         g_tau.set_far_field(tau_inf)
     err_s = err_t = 0.0
@@ -62,6 +64,8 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
             err_s = max(err_s, rel_l2(s, rs["s"]))
             err_t = max(err_t, rel_l2(t, rt["tau"]))
     assert g_tau.n == steps
+    g_tau.check()
+    g_s.check()
     g_tau.close()
     g_s.close()
     return err_s, err_t
@@ -72,18 +76,20 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
 @pytest.mark.parametrize("grid", [(4, 4, 400.0, 400.0), (16, 16, 1600.0, 1600.0),
                                   (8, 6, 800.0, 900.0)])
 @pytest.mark.parametrize("n_cut,side", [(1, 1), (5, -1), (32, 1)])
-def test_tiny_grids_brute_force(precision, kahan, grid, n_cut, side):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tiny_grids_brute_force(precision, kahan, grid, n_cut, side, variant):
     """Every mode, every lag, ring-buffer wrap-around (steps > n_cut), Nyquist
-    lines of white-spectrum input, square and rectangular grids."""
+    lines of white-spectrum input, square and rectangular grids; both
+    convolution variants (register prefetch, TMA staging)."""
     n1, n3, L1, L3 = grid
     steps = n_cut + 9
     es, et = run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan,
-                        seed=n1 + n_cut, spectrum="k2")
+                        seed=n1 + n_cut, spectrum="k2", variant=variant)
     assert es < TOL[precision], es
     assert et < TOL[precision], et
 
 
-@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0)])
+@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("fp32", 0)])
 def test_small_configuration(precision, kahan):
     """64 x 64 boundary, dx = 100 m, 256-lag cutoff, 200 steps of band-limited
     input: the small FP64 comparison case, every mode checked."""
@@ -132,6 +138,27 @@ def test_reset_restarts_history():
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("lags_per_cta", [1, 3, 7, 64])
+def test_explicit_lag_chunking(lags_per_cta):
+    """Tuner-chosen chunkings (one CTA per lag up to one CTA for all lags) give
+    the same traction up to float rounding."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    n, dx, n_cut = 16, 100.0, 40
+    dt = 0.3 * dx / CP
+    hist = separable_history(n, n, n * dx, n * dx, 50, dt, CS, seed=21)
+    ref = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, n_cut, 1, "fp32", True)
+    alt = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, n_cut, 1, "fp32", True)
+    alt.set_conv_config(1, lags_per_cta)
+    for m in range(50):
+        u = torch.from_numpy(hist.u(m).astype(np.float32)).cuda()
+        v = torch.from_numpy(hist.v(m).astype(np.float32)).cuda()
+        a = ref.step(u, v).double().cpu().numpy()
+        b = alt.step(u, v).double().cpu().numpy()
+        if np.linalg.norm(a) > 0:
+            assert rel_l2(b, a) < 2e-6
+    alt.check()
+
+
 def test_profiling_stage_times():
     from paper_2102_08756_gb300.sbim import SBIM
     n = 64
@@ -145,8 +172,9 @@ def test_profiling_stage_times():
     assert times["convolution"] > 0
 
 
-@pytest.mark.parametrize("precision,kahan,tol", [("fp32", 1, 1e-5), ("bf16x2", 1, 1e-4)])
-def test_large_boundary_sampled_modes(precision, kahan, tol):
+@pytest.mark.parametrize("precision,kahan,tol,variant", [("fp32", 1, 1e-5, 1), ("fp32", 1, 1e-5, 0),
+                                                         ("fp32", 0, 1e-5, 1), ("bf16x2", 1, 1e-4, 1)])
+def test_large_boundary_sampled_modes(precision, kahan, tol, variant):
     """1024 x 1024 boundary with the full 4096-lag history (plus wrap-around),
     in the launch configuration the benchmark times.  Input: two separable
     terms on 2 x 600 random Fourier bins with exactly known spectra; the last
@@ -160,6 +188,7 @@ def test_large_boundary_sampled_modes(precision, kahan, tol):
     hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=3003, n_terms=2,
                              spectrum="k2", sparse=600)
     g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
+    g.set_conv_config(variant)
     U = torch.from_numpy(hist.U.astype(np.float32)).cuda()
     gT = torch.from_numpy(hist.g.astype(np.float32))
     zero = torch.zeros((3, n3, n1), device="cuda")
@@ -169,7 +198,7 @@ def test_large_boundary_sampled_modes(precision, kahan, tol):
         torch.mul(U[0], float(gT[0, m]), out=u)
         u.add_(U[1], alpha=float(gT[1, m]))
         g.step(u, zero, tau)
-    torch.cuda.synchronize()
+    g.check()
     F_gpu = np.fft.rfft2(tau.double().cpu().numpy())
     g.close()
 
