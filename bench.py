@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 from paper_2102_08756_gb300.synth import config_large, separable_history  # noqa: E402
 
 MACS_PER_PAIR = 5
+DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 3, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
@@ -48,8 +49,11 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x2", "bf16"])
     p.add_argument("--kahan", type=int, default=1)
-    p.add_argument("--variant", type=int, default=1, help="convolution kernel: 1 TMA-staged, 0 register prefetch")
+    p.add_argument("--variant", type=int, default=-1,
+                   help="convolution kernel: -1 library default, 1-3 TMA-staged shapes, 0 register prefetch")
     p.add_argument("--lags-per-cta", type=int, default=0)
+    p.add_argument("--tune", action="store_true",
+                   help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,8 +94,10 @@ def peaks():
 
 
 def conv_src_sha1():
-    p = os.path.join(ROOT, "paper_2102_08756_gb300", "csrc", "sbim_conv.cu")
-    return hashlib.sha1(open(p, "rb").read()).hexdigest()
+    h = hashlib.sha1()
+    for f in ("sbim_conv_tma.cuh", "sbim_conv_tma_f32.cu", "sbim_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2102_08756_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 class ClockSampler:
@@ -242,7 +248,9 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     g = SBIM(n1, n3, c["L1"], c["L3"], c["cs"], c["cp"], c["rho"], dt, n_cut, 1, prec,
              bool(args.kahan), stream=stream)
-    g.set_conv_config(args.variant, args.lags_per_cta)
+    if args.variant >= 0 or args.lags_per_cta:
+        g.set_conv_config(args.variant if args.variant >= 0 else DEFAULT_VARIANT[prec],
+                          args.lags_per_cta)
     K, W = args.steps, args.warmup
     total_steps = n_cut + W + K
     hist = separable_history(n1, n3, c["L1"], c["L3"], total_steps + 1, dt, c["cs"],
@@ -272,6 +280,11 @@ def run_native(args):
     vs = [torch.empty_like(u) for _ in range(W + K)]
     for k in range(W + K):
         fields(n_cut + k, us[k], vs[k])
+    tuned = None
+    if args.tune:
+        from paper_2102_08756_gb300.tune import autotune
+        best, table = autotune(g, us[0], vs[0])
+        tuned = {"best": best, "trials": table}
     for k in range(W):
         g.step(us[k], vs[k], tau)
     torch.cuda.synchronize()
@@ -316,6 +329,7 @@ def run_native(args):
     peak, peak_kind = peaks()
     traffic = None
     if NCU_TRAFFIC["conv_src_sha1"] == conv_src_sha1() and prec == "fp32" and n1 == 1024 \
+            and args.variant in (-1, 2) and not args.lags_per_cta \
             and n_cut == 4096:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
 
@@ -366,13 +380,14 @@ def run_native(args):
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(c, prec, args.kahan), "n1": n1, "n3": n3,
                    "n_cut": n_cut, "precision": prec, "kahan": int(bool(args.kahan)),
-                   "conv_variant": "tma" if args.variant == 1 else "ldg",
+                   "conv_variant": args.variant if args.variant >= 0 else DEFAULT_VARIANT[prec],
                    "modes": modes, "history_bytes": hist_bytes,
                    "l2": "inputs larger than L2 (history ring buffer >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "conv_kernel", "peak_kind": peak_kind,
+                     "kernel": "conv_tma_kernel" if (args.variant != 0) else "conv_kernel",
+                     "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": conv_ms},
         "stage_ms_per_step": {k: v / nprof for k, v in stage.items()},
         "hbm_gbs_step": alg_bytes / (ms_step * 1e-3) / 1e9,
@@ -381,6 +396,8 @@ def run_native(args):
         "clocks": clk.summary(),
         "gpu_launches": 3 * K,
     }
+    if tuned is not None:
+        line["autotune"] = tuned
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -162,9 +162,14 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
 /*
  * sbim_set_conv_config -- launch configuration of the history convolution
  * (Section 2.3, the per-mode time convolution), the knob a tuner turns.
- *   variant       1 (default): history slots staged in shared memory by TMA bulk
- *                 copies, blocked compensated sums; 0: per-thread register
- *                 prefetch, per-term compensated sums
+ *   variant       1, 2, 3: history slots staged in shared memory by TMA bulk
+ *                 copies, blocked compensated sums; the three pipeline shapes are
+ *                 4 stages x 2 lags x 2 CTAs/SM, 3 x 2 x 3, 2 x 4 x 2 (FP32 / BF16
+ *                 hi-lo), 8 x 2 x 2, 6 x 2 x 3, 4 x 4 x 2 (BF16 hi-only),
+ *                 3 x 1, 4 x 1, 2 x 2 at 2 CTAs/SM (FP64); 0: per-thread register
+ *                 prefetch, per-term compensated sums.  Default: 2 for float and
+ *                 bf16 hi-only history, 3 for bf16 hi/lo, 1 for double (the
+ *                 fastest shapes measured on GB300 at 1024^2 x 4096).
  *   lags_per_cta  lags one CTA convolves (0 = automatic: ~16 waves of resident CTAs)
  * Both variants compute the same sums to within float rounding.  May reallocate
  * the lag-chunk partial buffer (synchronising the stream); on failure the
@@ -214,6 +219,68 @@ int sbim_check_device(sbim_handle h);
 int sbim_spectral_response_noalloc(int n1, int n3, double L1, double L3, double cs,
                                    double cp, double rho, double dt, int side, int n_lags,
                                    const void* uhat_hist, void* fhat, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Hybrid FEM-SBIM time step (Section 2.4) with an explicit FEM slab        */
+/* (Section 2.2) and a slip-weakening fault (Section 2.1).                   */
+/* ------------------------------------------------------------------------- */
+typedef struct sbim_hybrid_ctx* sbim_hybrid;
+
+/*
+ * sbim_hybrid_create -- a slab of n1 x n2 x n3 8-node hexahedra (cubes of side h,
+ * periodic in x1 and x3) between two SBIM half-spaces (Section 2.4, Neumann
+ * coupling) or free surfaces.
+ *   n1, n3      elements (= nodes) along x1, x3: even, the SBIM grids of S+ and S-
+ *   n2          element layers across the slab (even with a fault)
+ *   h           element size (m); the SBIM planes are n1 h x n3 h
+ *   cs, cp, rho material (homogeneous); dt time step; n_cut SBIM history cutoff
+ *   precision   SBIM_FP32 (float fields, float SBIM history with Kahan sums) or
+ *               SBIM_FP64
+ *   boundaries  1: SBIM half-spaces above (side +1) and below (side -1); 0: free
+ *   fault       1: the node plane at element layer n2/2 is split into two copies
+ *               (node layers n2/2 and n2/2 + 1); without sbim_hybrid_set_fault
+ *               the copies are welded by the stick traction
+ * Fields are [L][3][n3][n1] with L = n2 + 2 node layers (n2 + 1 without a fault),
+ * layer 0 at the bottom boundary (S-) and L-1 at the top (S+), in the perturbation
+ * formulation (departures from the prestressed equilibrium), starting at rest.
+ */
+int sbim_hybrid_create(sbim_hybrid* out, int n1, int n2, int n3, double h, double cs,
+                       double cp, double rho, double dt, int n_cut, int precision,
+                       int boundaries, int fault, void* stream);
+
+/*
+ * sbim_hybrid_set_fault -- linear slip-weakening law (Eq. (slipweak)) on the split
+ * plane: mu_s and tau0 are HOST arrays [n3][n1] (static friction coefficient and
+ * x1 shear prestress in Pa); mu_k, Dc (m), sigma0 (normal prestress, compression
+ * positive, Pa).  Fault strength sigma^n mu(delta), delta = |tangential slip|,
+ * sigma^n = sigma0 - tau_2; stick/slip on the shear traction vector (Eq. (stickslip)).
+ */
+int sbim_hybrid_set_fault(sbim_hybrid h, const double* mu_s, const double* tau0, double mu_k,
+                          double Dc, double sigma0);
+
+/* sbim_hybrid_set_state / get_state -- device pointers [L][3][n3][n1] of the handle's
+ * element type for u, v, a (NULL: zero on set, skip on get).  Stream-ordered. */
+int sbim_hybrid_set_state(sbim_hybrid h, const void* u, const void* v, const void* a);
+int sbim_hybrid_get_state(sbim_hybrid h, void* u, void* v, void* a);
+
+/*
+ * sbim_hybrid_step -- one hybrid time step (the seven steps of Section 2.4).
+ * force: optional device pointer [L][3][n3][n1], an external nodal force (N)
+ * added to f at t_{n+1}; NULL for none.  Stream-ordered, no host sync.
+ */
+int sbim_hybrid_step(sbim_hybrid h, const void* force);
+
+/* sbim_hybrid_fault_fields -- device outputs [3][n3][n1] (any may be NULL): slip
+ * vector u+ - u-, slip rate v+ - v-, and the fault traction perturbation of the
+ * last step (Pa). */
+int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* traction);
+
+/* sbim_hybrid_info -- node layers, steps taken, and the two SBIM handles (NULL
+ * with free surfaces), e.g. for profiling or sbim_set_conv_config. */
+int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* top,
+                     sbim_handle* bottom);
+
+int sbim_hybrid_destroy(sbim_hybrid h);
 
 /* sbim_destroy -- free everything the handle owns; NULL is accepted. */
 int sbim_destroy(sbim_handle h);

@@ -1,0 +1,40 @@
+// Internal declarations of the explicit FEM slab (Section 2.2) used by the
+// hybrid FEM-SBIM driver (Section 2.4).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sbim {
+namespace fem {
+
+struct MeshArgs {
+  int n1, n3, L;      // nodes along x1, x3; node layers
+  int f;              // minus-copy layer of the split fault plane
+  int fault;          // 1 if the plane at layer f is split
+  double area;        // h^2: nodal area of boundary and fault nodes
+  double half_mass;   // rho h^3 / 2: mass from the 4 elements on one side of a node
+  const void* stencil;  // [2][18][3][3] blocks (float or double, as the fields)
+};
+
+template <class R>
+struct FaultArgs {
+  const R* mu_s;      // [n3][n1] static friction coefficient
+  const R* tau0;      // [n3][n1] x1 shear prestress (Pa)
+  R mu_k, Dc, sigma0; // dynamic friction, slip-weakening distance (m), normal prestress (Pa)
+  R* traction;        // [3][n3][n1] output: fault traction perturbation (Pa), or NULL
+};
+
+template <class R> cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st);
+template <class R>
+cudaError_t force(const R* u, R* an, const MeshArgs& g, const R* tau_top, const R* tau_bot,
+                  const R* src, cudaStream_t st);
+template <class R>
+cudaError_t fault(const R* u, const R* vpred, const R* a, R* an, const MeshArgs& g,
+                  const FaultArgs<R>& fa, R dt, int weld, cudaStream_t st);
+template <class R> cudaError_t correct(R* v, R* a, const R* an, long long n, R dt, cudaStream_t st);
+template <class R>
+cudaError_t fault_fields(const R* u, const R* v, const MeshArgs& g, R* slip, R* rate,
+                         cudaStream_t st);
+
+}  // namespace fem
+}  // namespace sbim

@@ -1,0 +1,227 @@
+// Explicit FEM slab with a slip-weakening fault (Section 2.2) -- the volume part
+// of the hybrid time step of Section 2.4.
+//
+// Mesh: n1 x n2 x n3 cubes of side h, periodic in x1 and x3, node layers
+// l = 0 .. L-1 from the bottom; with a fault the node plane at element layer
+// f = n2/2 is split into layer f (minus copy, elements below) and f+1 (plus
+// copy, elements above).  Fields are [L][3][n3][n1] (x1 fastest), so each
+// layer is a [3][n3][n1] block that the SBIM entry points take directly.
+//
+// Homogeneous material on a regular mesh: K u is a 27-point stencil of 3x3
+// blocks.  It splits into the contribution of the four elements below a node
+// (offsets o2 in {-1, 0}) and of the four above (o2 in {0, +1}); a node layer
+// has elements below unless it is the bottom layer or the fault's plus copy,
+// and above unless it is the top layer or the fault's minus copy.  The 2 x 18
+// blocks are assembled on the host from the hexahedron stiffness.
+#include "../../include/sbim.h"
+#include "fem_internal.cuh"
+
+namespace sbim {
+namespace fem {
+
+namespace {
+
+
+// v_pred = v + dt a; u <- u + dt v + dt^2/2 a  (Eq. (fepred); central-difference
+// displacement update).  v is overwritten by v_pred.
+template <class R>
+__global__ void predict_kernel(R* __restrict__ u, R* __restrict__ v, const R* __restrict__ a,
+                               long long n, R dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R vi = v[i], ai = a[i];
+    u[i] += dt * vi + (R)0.5 * dt * dt * ai;
+    v[i] = vi + dt * ai;
+  }
+}
+
+// an = (-K u + f_boundary) / m: the acceleration without fault traction.
+// f_boundary = +A tau_top on the top layer, -A tau_bot on the bottom layer.
+template <class R>
+__global__ void force_kernel(const R* __restrict__ u, R* __restrict__ an, MeshArgs g,
+                             const R* __restrict__ tau_top, const R* __restrict__ tau_bot,
+                             const R* __restrict__ src) {
+  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i3 = blockIdx.y;
+  const int l = blockIdx.z;
+  if (i1 >= g.n1) return;
+  const long long plane = (long long)g.n1 * g.n3;
+  const R* __restrict__ S = reinterpret_cast<const R*>(g.stencil);
+  const bool down = l > 0 && !(g.fault && l == g.f + 1);
+  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+  R F[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? !down : !up) continue;
+    const int base = side * 18 * 9;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const int ly = l + (side == 0 ? oy - 1 : oy);
+      const R* ul = u + (long long)ly * 3 * plane;
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz) {
+        int j3 = i3 + oz - 1;
+        j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+          int j1 = i1 + ox - 1;
+          j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
+          const long long q = (long long)j3 * g.n1 + j1;
+          const R u0 = __ldg(ul + q), u1 = __ldg(ul + plane + q), u2 = __ldg(ul + 2 * plane + q);
+          const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            F[c] -= __ldg(S + s + 3 * c) * u0 + __ldg(S + s + 3 * c + 1) * u1 +
+                    __ldg(S + s + 3 * c + 2) * u2;
+        }
+      }
+    }
+  }
+  const long long q0 = (long long)i3 * g.n1 + i1;
+  if (l == g.L - 1 && tau_top)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[c] += g.area * tau_top[c * plane + q0];
+  if (l == 0 && tau_bot)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[c] -= g.area * tau_bot[c * plane + q0];
+  const R inv_m = (R)1 / ((down ? (R)g.half_mass : (R)0) + (up ? (R)g.half_mass : (R)0));
+  R* al = an + (long long)l * 3 * plane;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R extra = src ? src[((long long)l * 3 + c) * plane + q0] : (R)0;
+    al[c * plane + q0] = (F[c] + extra) * inv_m;
+  }
+}
+
+// Fault traction by the forward Lagrange-multiplier method (Eqs. (freeslip),
+// (sticktraction), (stickslip)) with linear slip weakening (Eq. (slipweak)), in
+// the perturbation formulation: shear traction tau0 + tau, normal stress
+// (compression positive) sigma0 - tau_2; the normal component always sticks.
+// Applies -A tau / m+ to the plus copy and +A tau / m- to the minus copy.
+template <class R>
+__global__ void fault_kernel(const R* __restrict__ u, const R* __restrict__ vpred,
+                             const R* __restrict__ a, R* __restrict__ an, MeshArgs g,
+                             FaultArgs<R> fa, R dt, int weld) {
+  const long long plane = (long long)g.n1 * g.n3;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const long long P = (long long)(g.f + 1) * 3 * plane + q;   // plus copy, component 0
+  const long long M = (long long)g.f * 3 * plane + q;         // minus copy
+  const R m = (R)g.half_mass;                                 // each copy: 4 elements
+  R stick[3], slipc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long o = c * plane;
+    const R vp = vpred[P + o] - (R)0.5 * dt * a[P + o] + dt * an[P + o];
+    const R vm = vpred[M + o] - (R)0.5 * dt * a[M + o] + dt * an[M + o];
+    stick[c] = (vp - vm) / (dt * (R)g.area * ((R)2 / m));
+    slipc[c] = u[P + o] - u[M + o];
+  }
+  R tau[3] = {stick[0], stick[1], stick[2]};
+  if (!weld) {
+    const R slip = sqrt(slipc[0] * slipc[0] + slipc[2] * slipc[2]);
+    const R mus = fa.mu_s[q];
+    const R fric = slip < fa.Dc ? mus - (mus - fa.mu_k) * slip / fa.Dc : fa.mu_k;
+    const R strength = (fa.sigma0 - stick[1]) * fric;
+    const R t1 = fa.tau0[q] + stick[0], t3 = stick[2];
+    const R mag = sqrt(t1 * t1 + t3 * t3);
+    if (mag > strength) {
+      const R s = strength / mag;
+      tau[0] = t1 * s - fa.tau0[q];
+      tau[2] = t3 * s;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long o = c * plane;
+    an[P + o] -= (R)g.area * tau[c] / m;
+    an[M + o] += (R)g.area * tau[c] / m;
+    if (fa.traction) fa.traction[o + q] = tau[c];
+  }
+}
+
+// v = v_pred + dt/2 (a_{t+1} - a_t)  (Eq. (fecorr)); a = a_{t+1}.
+template <class R>
+__global__ void correct_kernel(R* __restrict__ v, R* __restrict__ a, const R* __restrict__ an,
+                               long long n, R dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R anew = an[i];
+    v[i] += (R)0.5 * dt * (anew - a[i]);
+    a[i] = anew;
+  }
+}
+
+// slip vector, slip rate and (given) traction of the fault plane, [3][n3][n1]
+template <class R>
+__global__ void fault_fields_kernel(const R* __restrict__ u, const R* __restrict__ v, MeshArgs g,
+                                   R* __restrict__ slip, R* __restrict__ rate) {
+  const long long plane = (long long)g.n1 * g.n3;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const long long P = (long long)(g.f + 1) * 3 * plane + q;
+  const long long M = (long long)g.f * 3 * plane + q;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (slip) slip[c * plane + q] = u[P + c * plane] - u[M + c * plane];
+    if (rate) rate[c * plane + q] = v[P + c * plane] - v[M + c * plane];
+  }
+}
+
+unsigned grid1(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)(b > 152 * 32 ? 152 * 32 : b);
+}
+
+}  // namespace
+
+template <class R>
+cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st) {
+  predict_kernel<R><<<grid1(n, 256), 256, 0, st>>>(u, v, a, n, dt);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t force(const R* u, R* an, const MeshArgs& g, const R* tau_top, const R* tau_bot,
+                  const R* src, cudaStream_t st) {
+  const int tx = g.n1 >= 128 ? 128 : 32;
+  const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
+  force_kernel<R><<<grid, tx, 0, st>>>(u, an, g, tau_top, tau_bot, src);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t fault(const R* u, const R* vpred, const R* a, R* an, const MeshArgs& g,
+                  const FaultArgs<R>& fa, R dt, int weld, cudaStream_t st) {
+  const long long plane = (long long)g.n1 * g.n3;
+  fault_kernel<R><<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(u, vpred, a, an, g, fa, dt, weld);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t correct(R* v, R* a, const R* an, long long n, R dt, cudaStream_t st) {
+  correct_kernel<R><<<grid1(n, 256), 256, 0, st>>>(v, a, an, n, dt);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t fault_fields(const R* u, const R* v, const MeshArgs& g, R* slip, R* rate,
+                         cudaStream_t st) {
+  const long long plane = (long long)g.n1 * g.n3;
+  fault_fields_kernel<R><<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(u, v, g, slip, rate);
+  return cudaGetLastError();
+}
+
+#define SBIM_FEM_INST(R)                                                                     \
+  template cudaError_t predict<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
+  template cudaError_t force<R>(const R*, R*, const MeshArgs&, const R*, const R*, const R*, \
+                                cudaStream_t);                                               \
+  template cudaError_t fault<R>(const R*, const R*, const R*, R*, const MeshArgs&,           \
+                                const FaultArgs<R>&, R, int, cudaStream_t);                  \
+  template cudaError_t correct<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
+  template cudaError_t fault_fields<R>(const R*, const R*, const MeshArgs&, R*, R*, cudaStream_t);
+SBIM_FEM_INST(float)
+SBIM_FEM_INST(double)
+
+}  // namespace fem
+}  // namespace sbim

@@ -1,0 +1,328 @@
+// Host side of the hybrid FEM-SBIM time step (Section 2.4): an explicit FEM
+// slab between two SBIM half-spaces, staggered Neumann coupling, optional
+// slip-weakening fault on the mid-plane.  One sbim_hybrid_step enqueues on the
+// handle's stream:
+//   (1) FE predictor (Eq. (fepred), central-difference displacement update)
+//   (2)-(3) sbim_step of the top (side +1) and bottom (side -1) half-spaces with
+//       u_{t+1} and the predicted velocity of the boundary layers
+//   (4) internal force + boundary forces f = +A tau_top / -A tau_bot
+//   (5) fault traction (forward Lagrange multiplier, slip weakening)
+//   (6)-(7) acceleration increment and velocity correction (Eqs. (tintf), (fecorr))
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/sbim.h"
+#include "fem_internal.cuh"
+#include "sbim_internal.cuh"
+
+struct sbim_hybrid_ctx {
+  int n1 = 0, n2 = 0, n3 = 0, L = 0, prec = SBIM_FP32, boundaries = 1, fault = 1;
+  double h = 0, cs = 0, cp = 0, rho = 0, dt = 0;
+  cudaStream_t stream = nullptr;
+  sbim_handle top = nullptr, bot = nullptr;
+  void* u = nullptr;
+  void* v = nullptr;
+  void* a = nullptr;
+  void* an = nullptr;
+  void* tau_top = nullptr;
+  void* tau_bot = nullptr;
+  void* mu_s = nullptr;
+  void* tau0 = nullptr;
+  void* traction = nullptr;
+  void* stencil = nullptr;
+  double mu_k = 0, Dc = 1, sigma0 = 0;
+  bool have_law = false;
+  long long n = 0;
+  size_t rs = 4;
+  long long plane() const { return (long long)n1 * n3; }
+  long long elems() const { return (long long)L * 3 * plane(); }
+};
+
+namespace {
+
+int hfail(int code, const char* fmt, ...) {
+  char buf[400];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  sbim::set_last_error(buf);
+  return code;
+}
+
+#define HCU(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return hfail(e_ == cudaErrorMemoryAllocation ? SBIM_ERR_OOM : SBIM_ERR_CUDA,   \
+                   "%s: %s", #call, cudaGetErrorString(e_));                        \
+  } while (0)
+
+// 24 x 24 stiffness of a cube of side h, local node a = i + 2 j + 4 k along
+// (x1, x2, x3), 2 x 2 x 2 Gauss points, dof 3 a + c.
+void hex8_stiffness(double h, double lam, double mu, double K[24][24]) {
+  std::memset(K, 0, sizeof(double) * 576);
+  const double g = 1.0 / std::sqrt(3.0);
+  double D[6][6] = {};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) D[i][j] = lam + (i == j ? 2 * mu : 0.0);
+  D[3][3] = D[4][4] = D[5][5] = mu;
+  for (int gp = 0; gp < 8; ++gp) {
+    const double p[3] = {(gp & 1) ? g : -g, (gp & 2) ? g : -g, (gp & 4) ? g : -g};
+    double dN[8][3];
+    for (int a = 0; a < 8; ++a) {
+      const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+      const double f[3] = {1 + s[0] * p[0], 1 + s[1] * p[1], 1 + s[2] * p[2]};
+      dN[a][0] = s[0] * f[1] * f[2] / 8.0 * 2.0 / h;
+      dN[a][1] = s[1] * f[0] * f[2] / 8.0 * 2.0 / h;
+      dN[a][2] = s[2] * f[0] * f[1] / 8.0 * 2.0 / h;
+    }
+    double B[6][24] = {};
+    for (int a = 0; a < 8; ++a) {
+      B[0][3 * a] = dN[a][0];
+      B[1][3 * a + 1] = dN[a][1];
+      B[2][3 * a + 2] = dN[a][2];
+      B[3][3 * a] = dN[a][1]; B[3][3 * a + 1] = dN[a][0];
+      B[4][3 * a + 1] = dN[a][2]; B[4][3 * a + 2] = dN[a][1];
+      B[5][3 * a] = dN[a][2]; B[5][3 * a + 2] = dN[a][0];
+    }
+    const double w = std::pow(h / 2.0, 3);
+    for (int i = 0; i < 24; ++i)
+      for (int j = 0; j < 24; ++j) {
+        double s = 0.0;
+        for (int r = 0; r < 6; ++r)
+          for (int t = 0; t < 6; ++t) s += B[r][i] * D[r][t] * B[t][j];
+        K[i][j] += s * w;
+      }
+  }
+}
+
+// Stencil blocks: for side 0 (the 4 elements below a node, the node is their
+// top node j = 1) and side 1 (the 4 above, j = 0), offset (o1, o2, o3) with
+// o1, o3 in {-1, 0, 1} and o2 in {-1, 0} (below) or {0, 1} (above), the sum of
+// the 3x3 blocks K[node][neighbour] over the elements that contain both.
+void build_stencil(const double K[24][24], double* out) {
+  std::memset(out, 0, 324 * sizeof(double));
+  for (int side = 0; side < 2; ++side) {
+    const int js = side == 0 ? 1 : 0;
+    for (int di = 0; di < 2; ++di)
+      for (int dk = 0; dk < 2; ++dk) {
+        const int a = di + 2 * js + 4 * dk;
+        for (int ox = 0; ox < 3; ++ox)
+          for (int oy = 0; oy < 2; ++oy)
+            for (int oz = 0; oz < 3; ++oz) {
+              const int bi = di + ox - 1, bj = js + (side == 0 ? oy - 1 : oy), bk = dk + oz - 1;
+              if (bi < 0 || bi > 1 || bj < 0 || bj > 1 || bk < 0 || bk > 1) continue;
+              const int b = bi + 2 * bj + 4 * bk;
+              double* blk = out + side * 162 + ((ox * 2 + oy) * 3 + oz) * 9;
+              for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) blk[3 * c + d] += K[3 * a + c][3 * b + d];
+            }
+      }
+  }
+}
+
+sbim::fem::MeshArgs mesh_args(const sbim_hybrid_ctx* c) {
+  sbim::fem::MeshArgs g;
+  g.n1 = c->n1; g.n3 = c->n3; g.L = c->L; g.f = c->n2 / 2; g.fault = c->fault;
+  g.area = c->h * c->h;
+  g.half_mass = 0.5 * c->rho * c->h * c->h * c->h;
+  g.stencil = c->stencil;
+  return g;
+}
+
+template <class R>
+int step_impl(sbim_hybrid_ctx* c, const void* src) {
+  cudaStream_t st = c->stream;
+  const R dt = (R)c->dt;
+  const long long n = c->elems(), lay = 3 * c->plane();
+  R* u = (R*)c->u;
+  R* v = (R*)c->v;
+  R* a = (R*)c->a;
+  R* an = (R*)c->an;
+  HCU(sbim::fem::predict<R>(u, v, a, n, dt, st));
+  if (c->boundaries) {
+    int rc = sbim_step(c->top, u + (c->L - 1) * lay, v + (c->L - 1) * lay, c->tau_top);
+    if (rc != SBIM_OK) return rc;
+    rc = sbim_step(c->bot, u, v, c->tau_bot);
+    if (rc != SBIM_OK) return rc;
+  }
+  const sbim::fem::MeshArgs g = mesh_args(c);
+  HCU(sbim::fem::force<R>(u, an, g, c->boundaries ? (const R*)c->tau_top : nullptr,
+                          c->boundaries ? (const R*)c->tau_bot : nullptr, (const R*)src, st));
+  if (c->fault) {
+    sbim::fem::FaultArgs<R> fa;
+    fa.mu_s = (const R*)c->mu_s;
+    fa.tau0 = (const R*)c->tau0;
+    fa.mu_k = (R)c->mu_k;
+    fa.Dc = (R)c->Dc;
+    fa.sigma0 = (R)c->sigma0;
+    fa.traction = (R*)c->traction;
+    HCU(sbim::fem::fault<R>(u, v, a, an, g, fa, dt, c->have_law ? 0 : 1, st));
+  }
+  HCU(sbim::fem::correct<R>(v, a, an, n, dt, st));
+  ++c->n;
+  return SBIM_OK;
+}
+
+void hrelease(sbim_hybrid_ctx* c) {
+  if (!c) return;
+  sbim_destroy(c->top);
+  sbim_destroy(c->bot);
+  void* p[] = {c->u,     c->v,     c->a,        c->an,      c->tau_top,
+               c->tau_bot, c->mu_s, c->tau0, c->traction, c->stencil};
+  for (void* x : p)
+    if (x) cudaFree(x);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbim_hybrid_create(sbim_hybrid* out, int n1, int n2, int n3, double h, double cs, double cp,
+                       double rho, double dt, int n_cut, int precision, int boundaries,
+                       int fault, void* stream) {
+  if (!out) return hfail(SBIM_ERR_ARG, "out is NULL");
+  if (n1 < 2 || n3 < 2 || (n1 & 1) || (n3 & 1)) return hfail(SBIM_ERR_ARG, "n1, n3 must be even and >= 2");
+  if (n2 < 1 || (fault && (n2 < 2 || (n2 & 1))))
+    return hfail(SBIM_ERR_ARG, "n2 must be >= 1 (even and >= 2 with a fault)");
+  if (!(h > 0) || !(dt > 0) || !(rho > 0) || !(cs > 0) || !(cp > cs))
+    return hfail(SBIM_ERR_ARG, "need h, dt, rho, cs > 0 and cp > cs");
+  if (precision != SBIM_FP32 && precision != SBIM_FP64)
+    return hfail(SBIM_ERR_ARG, "the hybrid step supports SBIM_FP32 and SBIM_FP64");
+  sbim_hybrid_ctx* c = new sbim_hybrid_ctx;
+  c->n1 = n1; c->n2 = n2; c->n3 = n3; c->h = h; c->cs = cs; c->cp = cp; c->rho = rho; c->dt = dt;
+  c->prec = precision; c->boundaries = boundaries ? 1 : 0; c->fault = fault ? 1 : 0;
+  c->stream = (cudaStream_t)stream;
+  c->L = n2 + (c->fault ? 2 : 1);
+  c->rs = precision == SBIM_FP64 ? 8 : 4;
+  int rc = SBIM_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (rc != SBIM_OK) return;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) rc = hfail(SBIM_ERR_OOM, "cudaMalloc %zu bytes: %s", bytes, cudaGetErrorString(e));
+    else if (cudaMemsetAsync(*p, 0, bytes, c->stream) != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "memset");
+  };
+  const size_t fb = c->elems() * c->rs, pb = 3 * c->plane() * c->rs;
+  alloc(&c->u, fb); alloc(&c->v, fb); alloc(&c->a, fb); alloc(&c->an, fb);
+  alloc(&c->tau_top, pb); alloc(&c->tau_bot, pb); alloc(&c->traction, pb);
+  alloc(&c->mu_s, c->plane() * c->rs); alloc(&c->tau0, c->plane() * c->rs);
+  alloc(&c->stencil, 324 * c->rs);
+  if (rc == SBIM_OK && c->boundaries) {
+    rc = sbim_create(&c->top, n1, n3, n1 * h, n3 * h, cs, cp, rho, dt, n_cut, +1, precision, 1, stream);
+    if (rc == SBIM_OK)
+      rc = sbim_create(&c->bot, n1, n3, n1 * h, n3 * h, cs, cp, rho, dt, n_cut, -1, precision, 1, stream);
+  }
+  if (rc == SBIM_OK) {
+    double K[24][24], S[324];
+    const double mu = rho * cs * cs, lam = rho * cp * cp - 2 * mu;
+    hex8_stiffness(h, lam, mu, K);
+    build_stencil(K, S);
+    float Sf[324];
+    for (int i = 0; i < 324; ++i) Sf[i] = (float)S[i];
+    const void* src = precision == SBIM_FP64 ? (const void*)S : (const void*)Sf;
+    const cudaError_t e = cudaMemcpyAsync(c->stencil, src, 324 * c->rs, cudaMemcpyHostToDevice,
+                                          c->stream);
+    if (e != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "stencil upload: %s", cudaGetErrorString(e));
+    if (rc == SBIM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = hfail(SBIM_ERR_CUDA, "sync");
+  }
+  if (rc == SBIM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "sync");
+  if (rc != SBIM_OK) {
+    hrelease(c);
+    return rc;
+  }
+  *out = c;
+  return SBIM_OK;
+}
+
+int sbim_hybrid_set_fault(sbim_hybrid h, const double* mu_s, const double* tau0, double mu_k,
+                          double Dc, double sigma0) {
+  if (!h || !mu_s || !tau0) return hfail(SBIM_ERR_ARG, "NULL argument");
+  if (!h->fault) return hfail(SBIM_ERR_STATE, "the handle was created without a fault");
+  if (!(Dc > 0)) return hfail(SBIM_ERR_ARG, "Dc must be positive");
+  const long long np = h->plane();
+  std::vector<float> f1, f2;
+  const void* s1 = mu_s;
+  const void* s2 = tau0;
+  if (h->prec == SBIM_FP32) {
+    f1.assign(mu_s, mu_s + np);
+    f2.assign(tau0, tau0 + np);
+    s1 = f1.data();
+    s2 = f2.data();
+  }
+  HCU(cudaMemcpyAsync(h->mu_s, s1, np * h->rs, cudaMemcpyHostToDevice, h->stream));
+  HCU(cudaMemcpyAsync(h->tau0, s2, np * h->rs, cudaMemcpyHostToDevice, h->stream));
+  HCU(cudaStreamSynchronize(h->stream));
+  h->mu_k = mu_k; h->Dc = Dc; h->sigma0 = sigma0; h->have_law = true;
+  return SBIM_OK;
+}
+
+int sbim_hybrid_set_state(sbim_hybrid h, const void* u, const void* v, const void* a) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  const size_t fb = h->elems() * h->rs;
+  const void* src[3] = {u, v, a};
+  void* dst[3] = {h->u, h->v, h->a};
+  for (int i = 0; i < 3; ++i) {
+    if (src[i]) HCU(cudaMemcpyAsync(dst[i], src[i], fb, cudaMemcpyDeviceToDevice, h->stream));
+    else HCU(cudaMemsetAsync(dst[i], 0, fb, h->stream));
+  }
+  return SBIM_OK;
+}
+
+int sbim_hybrid_get_state(sbim_hybrid h, void* u, void* v, void* a) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  const size_t fb = h->elems() * h->rs;
+  void* dst[3] = {u, v, a};
+  const void* src[3] = {h->u, h->v, h->a};
+  for (int i = 0; i < 3; ++i)
+    if (dst[i]) HCU(cudaMemcpyAsync(dst[i], src[i], fb, cudaMemcpyDeviceToDevice, h->stream));
+  return SBIM_OK;
+}
+
+int sbim_hybrid_step(sbim_hybrid h, const void* force) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  return h->prec == SBIM_FP64 ? step_impl<double>(h, force) : step_impl<float>(h, force);
+}
+
+int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* traction) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  if (!h->fault) return hfail(SBIM_ERR_STATE, "the handle was created without a fault");
+  const sbim::fem::MeshArgs g = mesh_args(h);
+  cudaError_t e;
+  if (h->prec == SBIM_FP64)
+    e = sbim::fem::fault_fields<double>((const double*)h->u, (const double*)h->v, g,
+                                        (double*)slip, (double*)slip_rate, h->stream);
+  else
+    e = sbim::fem::fault_fields<float>((const float*)h->u, (const float*)h->v, g, (float*)slip,
+                                       (float*)slip_rate, h->stream);
+  if (e != cudaSuccess) return hfail(SBIM_ERR_CUDA, "fault fields: %s", cudaGetErrorString(e));
+  if (traction)
+    HCU(cudaMemcpyAsync(traction, h->traction, 3 * h->plane() * h->rs, cudaMemcpyDeviceToDevice,
+                        h->stream));
+  return SBIM_OK;
+}
+
+int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* top,
+                     sbim_handle* bottom) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  if (layers) *layers = h->L;
+  if (steps) *steps = h->n;
+  if (top) *top = h->top;
+  if (bottom) *bottom = h->bot;
+  return SBIM_OK;
+}
+
+int sbim_hybrid_destroy(sbim_hybrid h) {
+  if (!h) return SBIM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  hrelease(h);
+  return SBIM_OK;
+}
+
+}  // extern "C"

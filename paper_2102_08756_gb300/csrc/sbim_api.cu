@@ -105,7 +105,7 @@ struct sbim_ctx {
   double L1 = 0, L3 = 0, cs = 0, cp = 0, rho = 0, dt = 0, mu = 0, eta = 0;
   cudaStream_t stream = nullptr;
   int n_orb = 0, n_orb_pad = 0, lc = 1, nchunks = 1;
-  int variant = 1;            // 0: register-prefetch loads, 1: TMA-staged history
+  int variant = 1;            // 0: register-prefetch loads, 1-3: TMA-staged history shapes
   int lags_per_cta = 0;       // 0: automatic
   size_t part_bytes = 0;
   double tab_h = 0;
@@ -240,7 +240,7 @@ int choose_chunks(sbim_ctx& c) {
     c.lc = std::min(c.lags_per_cta, c.n_cut);
   } else {
     const long long tiles = c.n_orb_pad / sbim::kOrbitTile;
-    const int per_sm = c.variant == 1 ? sbim::conv_tma_ctas_per_sm(c.prec)
+    const int per_sm = c.variant >= 1 ? sbim::conv_tma_ctas_per_sm(c.prec, c.variant)
                                       : (c.prec == SBIM_FP64 ? 1 : 3);
     const long long target = (long long)sms * per_sm * 16;
     long long S = (target + tiles - 1) / tiles;
@@ -476,6 +476,10 @@ int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double c
   c->dt = dt; c->n_cut = n_cut; c->side = side; c->prec = precision;
   c->kahan = precision == SBIM_FP64 ? 0 : (kahan ? 1 : 0);
   c->stream = (cudaStream_t)stream;
+  // default convolution launch: the shapes the autotuner measured fastest on
+  // GB300 at 1024^2 x 4096 (3 stages x 2 lags x 3 CTAs/SM for float and bf16
+  // hi-only, 2 x 4 x 2 for bf16 hi/lo, 3 x 1 x 2 for double)
+  c->variant = precision == SBIM_FP64 ? 1 : (precision == SBIM_BF16X2 ? 3 : 2);
   const int rc = create_impl(c);
   if (rc != SBIM_OK) {
     const std::string msg = g_err;
@@ -514,8 +518,8 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
     CF(cufftExecR2C(c->plan_fwd, (cufftReal*)in, (cufftComplex*)c->d_uhat));
   if (e) CU(cudaEventRecord(e[1], st));
   const sbim::StepArgs a = step_args(c);
-  if (c->variant == 1)
-    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, st));
+  if (c->variant >= 1)
+    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st));
   else
     CU(sbim::launch_conv(a, c->prec, c->kahan, st));
   if (e) CU(cudaEventRecord(e[2], st));
@@ -594,7 +598,7 @@ int sbim_check_device(sbim_handle h) {
 
 int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
-  if (variant != 0 && variant != 1) return fail(SBIM_ERR_ARG, "variant must be 0 or 1");
+  if (variant < 0 || variant > 3) return fail(SBIM_ERR_ARG, "variant must be 0..3");
   if (lags_per_cta < 0) return fail(SBIM_ERR_ARG, "lags_per_cta must be >= 0");
   const int old_v = h->variant, old_l = h->lags_per_cta, old_lc = h->lc, old_nc = h->nchunks;
   h->variant = variant;

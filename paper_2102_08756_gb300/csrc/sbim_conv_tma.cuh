@@ -1,0 +1,337 @@
+// History convolution with the history slots staged in shared memory by TMA
+// bulk copies (Section 2.3, spectral evaluation of s_i: the per-mode truncated
+// time convolution, step A4).
+//
+// One CTA = one tile of 128 orbits (one thread per orbit) and one chunk of lags.
+// For every lag the tile's history lives in 3 contiguous segments of global
+// memory (one per component, 128 records each), so an elected thread stages a
+// pipeline stage of KS lags with 3 KS cp.async.bulk copies completing on an
+// mbarrier, NS stages deep; the bytes in flight cost no registers.  Threads read
+// their own 16-byte chunks from the staged segments with a per-quarter-warp
+// rotation of the chunk order that avoids shared-memory bank conflicts.
+//
+// The convolution weights of stage i+1 are prepared while stage i is computed:
+// the four kernel-table nodes of each of its lags are loaded before stage i's
+// arithmetic and interpolated after it, so the table's L1/L2 latency overlaps
+// the FMA chains.
+//
+// Compensated accumulation is blocked: the KS terms of one stage are chained by
+// FMAs starting from the negated compensation, then a single Kahan update folds
+// the block into the running sum (error ~ (KS + 2) eps sum|terms| instead of
+// ~2 eps for per-term Kahan, at well under half the instructions).
+//
+// Every mbarrier wait is bounded; a wait that gives up sets the device error
+// word, waits (bounded) for the copies this CTA still has in flight, and
+// returns without writing its partial sums.
+#pragma once
+
+#include "../../include/sbim.h"
+#include "sbim_device.cuh"
+
+namespace sbim {
+namespace tma {
+
+using namespace dev;
+
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+template <class S>
+__host__ __device__ constexpr int seg_bytes() { return kOrbitTile * S::kRecBytes; }
+template <class S, int KS>
+__host__ __device__ constexpr int stage_bytes() { return KS * 3 * S::kPlanes * seg_bytes<S>(); }
+template <class S, int NS, int KS>
+__host__ __device__ constexpr int smem_bytes() { return NS * stage_bytes<S, KS>(); }
+
+// The four table nodes of one lag, and their cubic Lagrange combination (the
+// two halves of dev::lag_weights, split so the loads can be issued early).
+template <class T4>
+__device__ __forceinline__ void fetch_nodes(const T4* __restrict__ tab, unsigned long long u,
+                                            T4 nd[4]) {
+  const unsigned i = (unsigned)(u >> 32);
+  nd[0] = ld_tab(tab + i);
+  nd[1] = ld_tab(tab + i + 1);
+  nd[2] = ld_tab(tab + i + 2);
+  nd[3] = ld_tab(tab + i + 3);
+}
+
+template <class R, class T4>
+__device__ __forceinline__ void interp_nodes(const T4 nd[4], unsigned long long u, R scale,
+                                             R w[4]) {
+  const R t = (R)(unsigned)(u & 0xffffffffull) * (R)2.3283064365386962890625e-10;
+  const R tm1 = t - (R)1, tm2 = t - (R)2, tp1 = t + (R)1;
+  const R sixth = scale * (R)(1.0 / 6.0), halfs = scale * (R)0.5;
+  const R l0 = -t * tm1 * tm2 * sixth;
+  const R l1 = tp1 * tm1 * tm2 * halfs;
+  const R l2 = -tp1 * t * tm2 * halfs;
+  const R l3 = tp1 * t * tm1 * sixth;
+  w[0] = l0 * nd[0].x + l1 * nd[1].x + l2 * nd[2].x + l3 * nd[3].x;
+  w[1] = l0 * nd[0].y + l1 * nd[1].y + l2 * nd[2].y + l3 * nd[3].y;
+  w[2] = l0 * nd[0].z + l1 * nd[1].z + l2 * nd[2].z + l3 * nd[3].z;
+  w[3] = l0 * nd[0].w + l1 * nd[1].w + l2 * nd[2].w + l3 * nd[3].w;
+}
+
+template <class S, int KAHAN, int NS, int KS, int MINB>
+__global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepArgs a) {
+  using R = typename S::real;
+  using C = typename S::cplx;
+  using T4 = typename S::tab4;
+  constexpr int SEG = seg_bytes<S>();
+  constexpr int STAGE = stage_bytes<S, KS>();
+  constexpr int MPC = S::kChunkMembers, NCH = S::kChunks;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[NS];
+
+  const int tid = threadIdx.x;
+  const int tile0 = blockIdx.x * kOrbitTile;
+  const int o = tile0 + tid;
+  const int chunk = blockIdx.y;
+  const long long n = *a.step;
+  const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
+  const int m0 = chunk * a.lc;
+  if (m0 >= n_valid) return;   // uniform over the CTA
+  const int m1 = min(m0 + a.lc, n_valid);
+  const int sn = (int)(n % a.n_cut);
+  const R dT = reinterpret_cast<const R*>(a.dT)[o];
+  const unsigned long long us = a.ustep[o];
+  const T4* tab = reinterpret_cast<const T4*>(a.table);
+  const long long orb = a.n_orb_pad;
+
+  // chunk rotation against bank conflicts: the 8 threads of a quarter warp read
+  // 8 different 16-byte bank groups.  Accumulator slot j holds member
+  // ((j / MPC + rot) % NCH) * MPC + j % MPC.
+  const int rot = (NCH == 2) ? ((tid >> 2) & 1) : (NCH == 4 ? ((tid >> 1) & 3) : 0);
+
+  R acc[4][kFields], cmp[4][kFields];
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int k = 0; k < kFields; ++k) { acc[g][k] = (R)0; cmp[g][k] = (R)0; }
+
+  int mf = m0;
+  if (m0 == 0) {  // lag 0: rotate the current spectra, write the ring slot, use them directly
+    C D[3][4];
+    rotate_current(a, o, D);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      S::store(a.hist, ((long long)sn * 3 + c) * orb + o, a.slot_stride, D[c]);
+      S::round(D[c]);
+    }
+    R w[4];
+    lag_weights(tab, 0ull, dT * (R)0.5, w);
+    C Dp[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < NCH; ++r)
+        if (rot == r) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Dp[c][j] = D[c][((j / MPC + r) % NCH) * MPC + j % MPC];
+        }
+    accumulate<KAHAN>(acc, cmp, w, Dp);
+    mf = 1;
+  }
+
+  const int nst = (m1 - mf + KS - 1) / KS;
+  if (nst > 0) {
+    if (tid == 0) {
+#pragma unroll
+      for (int b = 0; b < NS; ++b) mbar_init(smem_addr(&full[b]), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned char* hist = reinterpret_cast<const unsigned char*>(a.hist);
+    const long long plane_bytes = a.slot_stride * S::kRecBytes;
+    auto issue = [&](int s) {
+      const int b = s % NS;
+      const int mb = mf + s * KS;
+      const int kk = min(KS, m1 - mb);
+      const unsigned bar = smem_addr(&full[b]);
+      mbar_expect_tx(bar, (unsigned)(kk * 3 * S::kPlanes * SEG));
+      for (int k = 0; k < kk; ++k) {
+        int slot = sn - (mb + k);
+        if (slot < 0) slot += a.n_cut;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int pl = 0; pl < S::kPlanes; ++pl) {
+            const unsigned char* src =
+                hist + pl * plane_bytes + (((long long)slot * 3 + c) * orb + tile0) * S::kRecBytes;
+            const unsigned dst = smem_addr(smem + b * STAGE + ((k * 3 + c) * S::kPlanes + pl) * SEG);
+            bulk_g2s(dst, src, SEG, bar);
+          }
+      }
+    };
+    if (tid == 0)
+      for (int s = 0; s < min(NS - 1, nst); ++s) issue(s);
+
+    // weights of stage 0
+    R wn[KS][4];
+    {
+      T4 nd[KS][4];
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (mf + k < m1) fetch_nodes(tab, (unsigned long long)(mf + k) * us, nd[k]);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (mf + k < m1) {
+          interp_nodes(nd[k], (unsigned long long)(mf + k) * us, dT, wn[k]);
+        } else {
+          wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
+        }
+      }
+    }
+
+    bool ok = true;
+    int done = 0;   // stages consumed
+    for (int i = 0; i < nst; ++i) {
+      // The CTA-wide vote makes the give-up decision uniform and certifies that
+      // every thread has finished stage i-1, whose buffer is refilled next.
+      const bool landed = mbar_wait(smem_addr(&full[i % NS]), (unsigned)((i / NS) & 1));
+      if (!__syncthreads_and(landed)) {
+        ok = false;
+        break;
+      }
+      if (tid == 0 && i + NS - 1 < nst) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(i + NS - 1);
+      }
+      done = i + 1;
+      const int mb = mf + i * KS;
+      const int kk = min(KS, m1 - mb);
+      R w[KS][4];
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[k][q] = wn[k][q];
+      // table nodes of the next stage, in flight during this stage's arithmetic
+      const int mn = mb + KS;
+      T4 nd[KS][4];
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (mn + k < m1) fetch_nodes(tab, (unsigned long long)(mn + k) * us, nd[k]);
+
+      const unsigned char* stage = smem + (i % NS) * STAGE;
+#pragma unroll
+      for (int r = 0; r < NCH; ++r) {
+        const int ch = (r + rot) % NCH;
+        C D[KS][3][MPC];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (k < kk) {
+              S::chunk_smem(stage + (k * 3 + c) * S::kPlanes * SEG, SEG, tid, ch, D[k][c]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < MPC; ++j) D[k][c][j] = cmake<C>(0, 0);
+            }
+          }
+#pragma unroll
+        for (int j = 0; j < MPC; ++j) {
+          const int g = r * MPC + j;
+          // field -> (kernel, component): 11:xi, 33:perp, 22:2, 12:2, 12:xi (re, im)
+          constexpr int kern[kFields] = {0, 0, 2, 2, 1, 1, 3, 3, 3, 3};
+          constexpr int comp[kFields] = {0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) {
+            R y = KAHAN ? -cmp[g][f] : acc[g][f];
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+              const C d = D[k][comp[f]][j];
+              y = fma(w[k][kern[f]], (f & 1) ? d.y : d.x, y);
+            }
+            if (KAHAN) {
+              const R t = acc[g][f] + y;
+              cmp[g][f] = (t - acc[g][f]) - y;
+              acc[g][f] = t;
+            } else {
+              acc[g][f] = y;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (mn + k < m1) {
+          interp_nodes(nd[k], (unsigned long long)(mn + k) * us, dT, wn[k]);
+        } else {
+          wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
+        }
+      }
+    }
+    if (!ok) {
+      if (tid == 0) atomicExch(a.err, 1);
+      // let the copies still in flight land before the CTA's shared memory is released
+      const int issued = min(nst, done + NS - 1);
+      for (int s = done; s < issued; ++s)
+        mbar_wait(smem_addr(&full[s % NS]), (unsigned)((s / NS) & 1));
+      return;
+    }
+  }
+
+  R* part = reinterpret_cast<R*>(a.part);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int member = (((g / MPC) + rot) % NCH) * MPC + g % MPC;
+#pragma unroll
+    for (int k = 0; k < kFields; ++k)
+      part[((long long)chunk * (4 * kFields) + member * kFields + k) * orb + o] =
+          KAHAN ? acc[g][k] - cmp[g][k] : acc[g][k];
+  }
+}
+
+// Launch one instantiation (sets the dynamic shared-memory attribute once).
+template <class S, int KAHAN, int NS, int KS, int MINB>
+cudaError_t launch_shape(const StepArgs& a, cudaStream_t st) {
+  static bool attr_set = false;
+  constexpr int bytes = smem_bytes<S, NS, KS>();
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
+  conv_tma_kernel<S, KAHAN, NS, KS, MINB><<<grid, kOrbitTile, bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tma
+}  // namespace sbim

@@ -1,0 +1,24 @@
+// Instantiations of the TMA-staged history convolution for FP32 history
+// (Section 2.3, the per-mode truncated time convolution).  Shapes: pipeline
+// stages x lags per stage x resident CTAs per SM, 24 KB per stage (48 KB for
+// shape 3).
+#include "sbim_conv_tma.cuh"
+
+namespace sbim {
+
+template <int KAHAN>
+static cudaError_t shapes_f32(const StepArgs& a, int shape, cudaStream_t st) {
+  using S = dev::StoreF32;
+  switch (shape) {
+    case 1: return tma::launch_shape<S, KAHAN, 4, 2, 2>(a, st);
+    case 2: return tma::launch_shape<S, KAHAN, 3, 2, 3>(a, st);
+    case 3: return tma::launch_shape<S, KAHAN, 2, 4, 2>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_conv_tma_f32(const StepArgs& a, int kahan, int shape, cudaStream_t st) {
+  return kahan ? shapes_f32<1>(a, shape, st) : shapes_f32<0>(a, shape, st);
+}
+
+}  // namespace sbim

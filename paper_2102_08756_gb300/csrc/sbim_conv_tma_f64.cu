@@ -1,0 +1,18 @@
+// Instantiations of the TMA-staged history convolution for FP64 history
+// (Section 2.3, the per-mode truncated time convolution).  Shapes: pipeline
+// stages x lags per stage x resident CTAs per SM, 24 KB per stage.
+#include "sbim_conv_tma.cuh"
+
+namespace sbim {
+
+cudaError_t launch_conv_tma_f64(const StepArgs& a, int /*kahan*/, int shape, cudaStream_t st) {
+  using S = dev::StoreF64;
+  switch (shape) {
+    case 1: return tma::launch_shape<S, 0, 3, 1, 2>(a, st);
+    case 2: return tma::launch_shape<S, 0, 4, 1, 2>(a, st);
+    case 3: return tma::launch_shape<S, 0, 2, 2, 2>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sbim

@@ -56,8 +56,10 @@ cudaError_t launch_conv(const StepArgs& a, int precision, int kahan, cudaStream_
 // History convolution with TMA bulk-copy staging of the history slots in shared
 // memory (same inputs and outputs as launch_conv).  ctas_per_sm reports the
 // residency the launch is sized for.
-cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, cudaStream_t s);
-int conv_tma_ctas_per_sm(int precision);
+// shape 1..3 selects the pipeline (stages, lags per stage, CTAs per SM).
+cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
+                            cudaStream_t s);
+int conv_tma_ctas_per_sm(int precision, int shape);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
                             long long plane, const double coef[3], const double tau_inf[3],

@@ -51,13 +51,25 @@ def lib():
     L.sbim_check_device.argtypes = [vp]
     L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
+    L.sbim_hybrid_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, d, d, d, i, i, i, i, vp]
+    L.sbim_hybrid_set_fault.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), d, d, d]
+    L.sbim_hybrid_set_state.argtypes = [vp, vp, vp, vp]
+    L.sbim_hybrid_get_state.argtypes = [vp, vp, vp, vp]
+    L.sbim_hybrid_step.argtypes = [vp, vp]
+    L.sbim_hybrid_fault_fields.argtypes = [vp, vp, vp, vp]
+    L.sbim_hybrid_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ll),
+                                   ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.sbim_hybrid_destroy.argtypes = [vp]
     L.sbim_last_error.argtypes = []
     L.sbim_last_error.restype = ctypes.c_char_p
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
                  "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
                  "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device",
-                 "sbim_spectral_response_noalloc", "sbim_destroy"):
+                 "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
+                 "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
+                 "sbim_hybrid_step", "sbim_hybrid_fault_fields", "sbim_hybrid_info",
+                 "sbim_hybrid_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -144,6 +156,46 @@ def sbim_last_error():
     return lib().sbim_last_error().decode()
 
 
+def sbim_hybrid_create(n1, n2, n3, h, cs, cp, rho, dt, n_cut, precision, boundaries, fault,
+                       stream):
+    hh = ctypes.c_void_p()
+    _check(lib().sbim_hybrid_create(ctypes.byref(hh), n1, n2, n3, h, cs, cp, rho, dt, n_cut,
+                                    precision, boundaries, fault, stream))
+    return hh
+
+
+def sbim_hybrid_set_fault(h, mu_s_ptr, tau0_ptr, mu_k, Dc, sigma0):
+    _check(lib().sbim_hybrid_set_fault(h, mu_s_ptr, tau0_ptr, mu_k, Dc, sigma0))
+
+
+def sbim_hybrid_set_state(h, u_ptr, v_ptr, a_ptr):
+    _check(lib().sbim_hybrid_set_state(h, u_ptr, v_ptr, a_ptr))
+
+
+def sbim_hybrid_get_state(h, u_ptr, v_ptr, a_ptr):
+    _check(lib().sbim_hybrid_get_state(h, u_ptr, v_ptr, a_ptr))
+
+
+def sbim_hybrid_step(h, force_ptr=None):
+    _check(lib().sbim_hybrid_step(h, force_ptr))
+
+
+def sbim_hybrid_fault_fields(h, slip_ptr, rate_ptr, traction_ptr):
+    _check(lib().sbim_hybrid_fault_fields(h, slip_ptr, rate_ptr, traction_ptr))
+
+
+def sbim_hybrid_info(h):
+    layers, steps = ctypes.c_int(), ctypes.c_longlong()
+    top, bot = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().sbim_hybrid_info(h, ctypes.byref(layers), ctypes.byref(steps),
+                                  ctypes.byref(top), ctypes.byref(bot)))
+    return layers.value, steps.value, top, bot
+
+
+def sbim_hybrid_destroy(h):
+    _check(lib().sbim_hybrid_destroy(h))
+
+
 # --- torch-facing wrapper ------------------------------------------------------
 class SBIM:
     """One half-space boundary (Section 2.3, Eq. (SBI)) on an n1 x n3 periodic grid.
@@ -158,6 +210,7 @@ class SBIM:
         self.torch = torch
         self.n1, self.n3, self.n_cut, self.side = n1, n3, n_cut, side
         self.precision = precision
+        self.kahan = kahan
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         if stream is None:
             stream = torch.cuda.current_stream()

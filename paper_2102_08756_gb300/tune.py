@@ -1,0 +1,63 @@
+"""Autotuner of the history-convolution launch (Section 2.3, the per-mode
+truncated time convolution): picks the kernel variant (register prefetch, or
+one of the TMA pipeline shapes) and the lags per CTA for a live handle by
+timing the convolution stage with the library's own per-stage CUDA events.
+
+Each trial runs real steps of the handle, so its history advances; tune a
+handle whose history is already representative (for the full-history cost,
+after n_cut steps).  Results can be cached in a JSON file keyed by grid,
+history length, precision, compensation and GPU name.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+VARIANTS = (1, 2, 3, 0)
+
+
+def _key(h, gpu_name):
+    return f"{h.n1}x{h.n3}:{h.n_cut}:{h.precision}:{int(bool(h.kahan))}:{gpu_name}"
+
+
+def autotune(h, u, v, steps=6, chunkings=None, cache=None, verbose=False):
+    """Time every (variant, lags_per_cta) candidate on handle ``h`` with the
+    input fields (u, v) and keep the fastest.  Returns (best, table)."""
+    gpu = torch.cuda.get_device_name(h.device)
+    if cache and os.path.exists(cache):
+        db = json.load(open(cache))
+        hit = db.get(_key(h, gpu))
+        if hit:
+            h.set_conv_config(hit["variant"], hit["lags_per_cta"])
+            return hit, None
+    if chunkings is None:
+        chunkings = sorted({0} | {c for c in (256, 512, 1024, 2048) if c < h.n_cut})
+    tau = torch.empty_like(u)
+    table = []
+    for var in VARIANTS:
+        for lpc in chunkings:
+            try:
+                h.set_conv_config(var, lpc)
+            except RuntimeError:
+                continue
+            h.step(u, v, tau)                     # warm-up of this launch shape
+            h.set_profiling(True)
+            for _ in range(steps):
+                h.step(u, v, tau)
+            times, n = h.stage_times()
+            h.set_profiling(False)
+            h.check()
+            row = {"variant": var, "lags_per_cta": lpc, "conv_ms": times["convolution"] / n}
+            table.append(row)
+            if verbose:
+                print(row, flush=True)
+    best = min(table, key=lambda r: r["conv_ms"])
+    h.set_conv_config(best["variant"], best["lags_per_cta"])
+    if cache:
+        db = json.load(open(cache)) if os.path.exists(cache) else {}
+        db[_key(h, gpu)] = best
+        with open(cache, "w") as f:
+            json.dump(db, f, indent=1)
+    return best, table

@@ -1,0 +1,119 @@
+"""GPU hybrid FEM-SBIM step (Sections 2.1, 2.2, 2.4) against the FP64 oracle,
+through the C ABI, and the non-reflection check of the coupled GPU path."""
+import numpy as np
+import pytest
+
+from oracle.fem_oracle import FaultLaw, HybridOracle, SlabMesh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CS, CP, RHO = 3464.0, 6000.0, 2670.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
+@pytest.mark.parametrize("fault,boundaries", [(False, True), (True, True), (True, False)])
+def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
+    """Random initial state, SBIM or free boundaries, welded split plane or none:
+    u, v, a after 30 steps equal the oracle's."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n1, n2, n3, h, n_cut, steps = 8, 4, 6, 50.0, 12, 30
+    dt = 0.3 * h / CP
+    me = SlabMesh(n1, n2, n3, h, fault=fault)
+    o = HybridOracle(me, CS, CP, RHO, dt, n_cut=n_cut, sbim=boundaries)
+    rng = np.random.default_rng(3)
+    o.u = rng.normal(size=o.u.shape) * 1e-3
+    o.v = rng.normal(size=o.u.shape) * 1e-2
+    if fault:
+        o.u[me.f + 1] = o.u[me.f]
+        o.v[me.f + 1] = o.v[me.f]
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, n_cut, precision, boundaries, fault)
+    g.set_state(torch.from_numpy(o.u).to("cuda", dtype), torch.from_numpy(o.v).to("cuda", dtype),
+                None)
+    for _ in range(steps):
+        o.step()
+        g.step()
+    u, v, a = (x.double().cpu().numpy() for x in g.get_state())
+    assert rel(u, o.u) < tol
+    assert rel(v, o.v) < tol * 10
+    assert rel(a, o.a) < tol * 10
+    g.close()
+
+
+def _rupture_setup(n1, n3):
+    i3, i1 = np.meshgrid(np.arange(n3), np.arange(n1), indexing="ij")
+    patch = (np.abs(i1 - n1 / 2 + 0.5) < 3) & (np.abs(i3 - n3 / 2 + 0.5) < 3)
+    mu_s = np.full((n3, n1), 0.677)
+    tau0 = np.where(patch, 1.005 * 0.677 * 120e6, 70e6)
+    return mu_s, tau0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 3e-3)])
+def test_rupture_matches_oracle(precision, tol):
+    """Slip-weakening rupture from an overstressed patch (TPV3-like stresses,
+    Dc scaled to the small fault): the slip-rate field over 45 steps."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n1 = n3 = 32
+    n2, h, steps = 4, 100.0, 45
+    dt = 0.3 * h / CP
+    mu_s, tau0 = _rupture_setup(n1, n3)
+    me = SlabMesh(n1, n2, n3, h, fault=True)
+    o = HybridOracle(me, CS, CP, RHO, dt, n_cut=steps + 1,
+                     fault=FaultLaw(mu_s, 0.525, 0.02, tau0, 120e6))
+    g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, precision, True, True)
+    g.set_fault(mu_s, tau0, 0.525, 0.02, 120e6)
+    worst, peak = 0.0, 0.0
+    for _ in range(steps):
+        o.step()
+        g.step()
+        slip, rate, trac = (x.double().cpu().numpy() for x in g.fault_fields())
+        peak = max(peak, np.abs(o.slip_rate).max())
+        if np.linalg.norm(o.slip_rate) > 0:
+            worst = max(worst, rel(rate, o.slip_rate))
+    assert peak > 1.0
+    assert worst < tol, worst
+    g.close()
+
+
+def test_gpu_sbim_boundaries_reproduce_an_unbounded_slab():
+    """The coupled GPU path: a force pulse in a thin slab with SBIM half-spaces
+    moves like the same pulse in a thick free slab until reflections return."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n1 = n3 = 16
+    n2, pad, h, steps = 8, 16, 50.0, 60
+    dt = 0.3 * h / CP
+    i3, i1 = np.meshgrid(np.arange(n3), np.arange(n1), indexing="ij")
+
+    def source(layers, first, n):
+        out = np.zeros((layers, 3, n3, n1), dtype=np.float32)
+        if n <= 12:
+            L = np.arange(layers)[:, None, None] - first
+            g = np.exp(-((i1 - n1 / 2) ** 2 + (i3 - n3 / 2) ** 2 + (L - n2 / 2) ** 2) / 4.5)
+            amp = np.sin(np.pi * n / 12) ** 2 * 1e9
+            out[:, 1] = amp * g
+            out[:, 0] = 0.5 * amp * g
+        return torch.from_numpy(out).cuda()
+
+    thin = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, "fp32", True, False)
+    thick = Hybrid(n1, n2 + 2 * pad, n3, h, CS, CP, RHO, dt, steps + 1, "fp32", False, False)
+    worst = 0.0
+    for n in range(1, steps + 1):
+        thin.step(source(n2 + 1, 0, n))
+        thick.step(source(n2 + 2 * pad + 1, pad, n))
+        ut = thin.get_state()[0].double().cpu().numpy()
+        ur = thick.get_state()[0].double().cpu().numpy()[pad:pad + n2 + 1]
+        worst = max(worst, rel(ut, ur))
+    assert worst < 0.08, worst

@@ -89,6 +89,19 @@ def test_tiny_grids_brute_force(precision, kahan, grid, n_cut, side, variant):
     assert et < TOL[precision], et
 
 
+@pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1), ("fp32", 0),
+                                             ("bf16x2", 1), ("bf16", 0), ("bf16", 1)])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_tma_pipeline_shapes(precision, kahan, variant):
+    """The other TMA pipeline shapes (deeper / wider stages, more CTAs per SM)
+    with ring-buffer wrap-around and both half-spaces."""
+    for side, n_cut in ((1, 13), (-1, 40)):
+        es, et = run_parity(16, 12, 1600.0, 1200.0, n_cut, side, n_cut + 11, precision, kahan,
+                            seed=variant + n_cut, spectrum="k2", variant=variant)
+        assert es < TOL[precision], es
+        assert et < TOL[precision], et
+
+
 @pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("fp32", 0)])
 def test_small_configuration(precision, kahan):
     """64 x 64 boundary, dx = 100 m, 256-lag cutoff, 200 steps of band-limited
