@@ -38,7 +38,7 @@ DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 3, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"conv_src_sha1": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"conv_src_sha1": "7ebcc73cd57143cff62d6a79996ddfe96205df72", "bytes_per_launch": 52.16e9 + 183.56e6}
 
 
 def parse():
@@ -56,6 +56,9 @@ def parse():
                    help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
+    p.add_argument("--workload", default="sbim", choices=["sbim", "coupled"],
+                   help="sbim: the single half-space update (default); coupled: FEM slab + fault "
+                        "between two half-spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -403,12 +406,73 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+def run_coupled(args):
+    """Coupled hybrid step: an explicit 512 x 16 x 512 hexahedral slab (dx = 100 m)
+    with a planar slip-weakening fault at mid-depth (mu_s 0.677, mu_k 0.525,
+    Dc 0.4 m, tau0 70 MPa, sigma0 120 MPa, a 3 km square patch at 1.005 mu_s
+    sigma0, breakable over 30 km x 15 km) between two SBIM half-spaces with
+    2000-lag FP32 histories.  The rupture runs from rest; the timed steps follow
+    the n_cut steps that fill the histories."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2102_08756_gb300 import _build
+    _build.build()
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n1 = n3 = args.n or 512
+    n2, h, cs, cp, rho = 16, 100.0, 3464.0, 6000.0, 2670.0
+    n_cut = args.n_cut or 2000
+    dt = 0.3 * h / cp
+    g = Hybrid(n1, n2, n3, h, cs, cp, rho, dt, n_cut, "fp32", True, True)
+    x1 = (np.arange(n1) - n1 / 2 + 0.5) * h
+    x3 = (np.arange(n3) - n3 / 2 + 0.5) * h
+    X3, X1 = np.meshgrid(x3, x1, indexing="ij")
+    breakable = (np.abs(X1) <= 15e3) & (np.abs(X3) <= 7.5e3)
+    patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
+    mu_s = np.where(breakable, 0.677, 1e4)
+    tau0 = np.where(patch, 1.005 * 0.677 * 120e6, 70e6)
+    g.set_fault(mu_s, tau0, 0.525, 0.4, 120e6)
+    K, W = args.steps, args.warmup
+    for _ in range(n_cut + W):
+        g.step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(K):
+            g.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    slip, rate, _ = g.fault_fields()
+    modes = n3 * (n1 // 2 + 1)
+    macs = 2 * modes * n_cut * MACS_PER_PAIR
+    line = {
+        "metric": "coupled hybrid steps/s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
+        "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"hybrid FEM-SBIM, {n1}x{n2}x{n3} hex slab dx=100 m, planar "
+                               f"slip-weakening fault, two SBIM half-spaces, {n_cut}-lag history",
+                   "elements": n1 * n2 * n3, "l2": "history (12.6 GB) >> L2"},
+        "sbim_macs_per_s": macs / (ms * 1e-3),
+        "fault": {"max_slip_m": float(slip.abs().max()), "max_slip_rate_m_s": float(rate.abs().max()),
+                  "simulated_s": (n_cut + W + K) * dt},
+        "clocks": clk.summary(),
+    }
+    g.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "coupled":
+        run_coupled(args)
     else:
         run_native(args)
 
