@@ -221,6 +221,48 @@ int sbim_spectral_response_noalloc(int n1, int n3, double L1, double L3, double 
                                    const void* uhat_hist, void* fhat, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Batches of independent updates (Section 2.3) with ragged grids           */
+/* ------------------------------------------------------------------------- */
+typedef struct sbim_batch_ctx* sbim_batch;
+
+/*
+ * sbim_batch_create -- nb independent half-spaces (Eq. (SBI) each), member i with
+ * its own grid n1[i] x n3[i], lengths, material, dt, cutoff n_cut[i] and side[i]
+ * (arrays of nb HOST values), one precision (SBIM_FP32 / BF16 variants), one
+ * compensation flag and one stream.  The members are handles the batch owns
+ * (reachable through sbim_batch_member).  A batch step runs the FFTs and the
+ * epilogue per member and the history convolution of ALL members in one
+ * persistent launch over their (member, orbit tile, 256-lag chunk) items, taken
+ * from a work counter; each item writes its own partial sums, so results do not
+ * depend on the schedule.  The batch sets its members' convolution launch
+ * (sbim_set_conv_config) to the pipeline shape of the persistent kernel (3 for
+ * float history, 1 for bf16) and 256 lags per chunk.
+ */
+int sbim_batch_create(sbim_batch* out, int nb, const int* n1, const int* n3, const double* L1,
+                      const double* L3, const double* cs, const double* cp, const double* rho,
+                      const double* dt, const int* n_cut, const int* side, int precision,
+                      int kahan, void* stream);
+
+/* sbim_batch_step -- one update of every member: u, v, tau are HOST arrays of nb
+ * DEVICE pointers ([3][n3[i]][n1[i]] each), as for sbim_step.  Stream-ordered. */
+int sbim_batch_step(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
+
+/*
+ * sbim_batch_capture / sbim_batch_replay -- capture one batch step with these
+ * (fixed) buffers into a CUDA graph on the batch's stream (which must not be the
+ * legacy default stream), then replay it: each replay is one step of every
+ * member, reading whatever the buffers hold at that point of the stream.  The
+ * capture itself enqueues no work.  Re-capturing replaces the graph.
+ */
+int sbim_batch_capture(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
+int sbim_batch_replay(sbim_batch b);
+
+/* sbim_batch_member -- the handle of member i (owned by the batch). */
+int sbim_batch_member(sbim_batch b, int i, sbim_handle* h);
+
+int sbim_batch_destroy(sbim_batch b);
+
+/* ------------------------------------------------------------------------- */
 /* Hybrid FEM-SBIM time step (Section 2.4) with an explicit FEM slab        */
 /* (Section 2.2) and a slip-weakening fault (Section 2.1).                   */
 /* ------------------------------------------------------------------------- */
@@ -281,6 +323,22 @@ int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* 
                      sbim_handle* bottom);
 
 int sbim_hybrid_destroy(sbim_hybrid h);
+
+/*
+ * Ensembles of independent hybrid scenarios (ragged grids, slab thicknesses,
+ * fault laws, cutoffs): sbim_hybrid_batch_create groups existing hybrid handles
+ * (SBIM boundaries, SBIM_FP32, one shared stream; not owned by the batch).  A
+ * batch step runs every member's FE stages and ONE batched SBIM step over all
+ * 2 nb half-spaces (sbim_batch: one persistent convolution launch).  capture /
+ * replay put one batch step in a CUDA graph on the shared (non-default) stream.
+ * Destroy the batch before its members.
+ */
+typedef struct sbim_hybrid_batch_ctx* sbim_hybrid_batch;
+int sbim_hybrid_batch_create(sbim_hybrid_batch* out, int nb, const sbim_hybrid* members);
+int sbim_hybrid_batch_step(sbim_hybrid_batch b);
+int sbim_hybrid_batch_capture(sbim_hybrid_batch b);
+int sbim_hybrid_batch_replay(sbim_hybrid_batch b);
+int sbim_hybrid_batch_destroy(sbim_hybrid_batch b);
 
 /* sbim_destroy -- free everything the handle owns; NULL is accepted. */
 int sbim_destroy(sbim_handle h);

@@ -41,6 +41,13 @@ struct sbim_hybrid_ctx {
   long long elems() const { return (long long)L * 3 * plane(); }
 };
 
+struct sbim_hybrid_batch_ctx {
+  std::vector<sbim_hybrid> m;
+  sbim_batch sb = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 int hfail(int code, const char* fmt, ...) {
@@ -134,22 +141,33 @@ sbim::fem::MeshArgs mesh_args(const sbim_hybrid_ctx* c) {
   return g;
 }
 
+// Stage (1): FE predictor.
 template <class R>
-int step_impl(sbim_hybrid_ctx* c, const void* src) {
+int stage_predict(sbim_hybrid_ctx* c) {
+  HCU(sbim::fem::predict<R>((R*)c->u, (R*)c->v, (const R*)c->a, c->elems(), (R)c->dt, c->stream));
+  return SBIM_OK;
+}
+
+// Boundary layers handed to the SBIM half-spaces (top: last layer, bottom: first).
+void boundary_ptrs(sbim_hybrid_ctx* c, const void** u_top, const void** v_top,
+                   const void** u_bot, const void** v_bot) {
+  const long long lay = 3 * c->plane() * (long long)c->rs;
+  *u_top = (const char*)c->u + (c->L - 1) * lay;
+  *v_top = (const char*)c->v + (c->L - 1) * lay;
+  *u_bot = c->u;
+  *v_bot = c->v;
+}
+
+// Stages (4)-(7): forces, fault traction, acceleration increment, correction.
+template <class R>
+int stage_finish(sbim_hybrid_ctx* c, const void* src) {
   cudaStream_t st = c->stream;
   const R dt = (R)c->dt;
-  const long long n = c->elems(), lay = 3 * c->plane();
+  const long long n = c->elems();
   R* u = (R*)c->u;
   R* v = (R*)c->v;
   R* a = (R*)c->a;
   R* an = (R*)c->an;
-  HCU(sbim::fem::predict<R>(u, v, a, n, dt, st));
-  if (c->boundaries) {
-    int rc = sbim_step(c->top, u + (c->L - 1) * lay, v + (c->L - 1) * lay, c->tau_top);
-    if (rc != SBIM_OK) return rc;
-    rc = sbim_step(c->bot, u, v, c->tau_bot);
-    if (rc != SBIM_OK) return rc;
-  }
   const sbim::fem::MeshArgs g = mesh_args(c);
   HCU(sbim::fem::force<R>(u, an, g, c->boundaries ? (const R*)c->tau_top : nullptr,
                           c->boundaries ? (const R*)c->tau_bot : nullptr, (const R*)src, st));
@@ -164,8 +182,23 @@ int step_impl(sbim_hybrid_ctx* c, const void* src) {
     HCU(sbim::fem::fault<R>(u, v, a, an, g, fa, dt, c->have_law ? 0 : 1, st));
   }
   HCU(sbim::fem::correct<R>(v, a, an, n, dt, st));
-  ++c->n;
   return SBIM_OK;
+}
+
+template <class R>
+int step_impl(sbim_hybrid_ctx* c, const void* src) {
+  int rc = stage_predict<R>(c);
+  if (rc != SBIM_OK) return rc;
+  if (c->boundaries) {
+    const void *ut, *vt, *ub, *vb;
+    boundary_ptrs(c, &ut, &vt, &ub, &vb);
+    rc = sbim_step(c->top, ut, vt, c->tau_top);
+    if (rc == SBIM_OK) rc = sbim_step(c->bot, ub, vb, c->tau_bot);
+    if (rc != SBIM_OK) return rc;
+  }
+  rc = stage_finish<R>(c, src);
+  if (rc == SBIM_OK) ++c->n;
+  return rc;
 }
 
 void hrelease(sbim_hybrid_ctx* c) {
@@ -314,6 +347,106 @@ int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* 
   if (steps) *steps = h->n;
   if (top) *top = h->top;
   if (bottom) *bottom = h->bot;
+  return SBIM_OK;
+}
+
+int sbim_hybrid_batch_create(sbim_hybrid_batch* out, int nb, const sbim_hybrid* members) {
+  if (!out || nb < 1 || !members) return hfail(SBIM_ERR_ARG, "bad batch arguments");
+  for (int i = 0; i < nb; ++i) {
+    if (!members[i]) return hfail(SBIM_ERR_ARG, "NULL member %d", i);
+    if (!members[i]->boundaries || members[i]->prec != SBIM_FP32)
+      return hfail(SBIM_ERR_ARG, "batch members need SBIM boundaries and SBIM_FP32");
+    if (members[i]->stream != members[0]->stream)
+      return hfail(SBIM_ERR_ARG, "batch members must share one stream");
+  }
+  sbim_hybrid_batch_ctx* b = new sbim_hybrid_batch_ctx;
+  b->m.assign(members, members + nb);
+  std::vector<sbim_handle> hs;
+  for (sbim_hybrid x : b->m) {
+    hs.push_back(x->top);
+    hs.push_back(x->bot);
+  }
+  const int rc = sbim::batch_from_handles(&b->sb, hs.data(), (int)hs.size());
+  if (rc != SBIM_OK) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return SBIM_OK;
+}
+
+namespace {
+int hbatch_enqueue(sbim_hybrid_batch b) {
+  for (sbim_hybrid x : b->m) {
+    const int rc = stage_predict<float>(x);
+    if (rc != SBIM_OK) return rc;
+  }
+  std::vector<const void*> u, v;
+  std::vector<void*> tau;
+  for (sbim_hybrid x : b->m) {
+    const void *ut, *vt, *ub, *vb;
+    boundary_ptrs(x, &ut, &vt, &ub, &vb);
+    u.push_back(ut); v.push_back(vt); tau.push_back(x->tau_top);
+    u.push_back(ub); v.push_back(vb); tau.push_back(x->tau_bot);
+  }
+  int rc = sbim::batch_enqueue(b->sb, u.data(), v.data(), tau.data());
+  if (rc != SBIM_OK) return rc;
+  for (sbim_hybrid x : b->m) {
+    rc = stage_finish<float>(x, nullptr);
+    if (rc != SBIM_OK) return rc;
+  }
+  return SBIM_OK;
+}
+void hbatch_advance(sbim_hybrid_batch b) {
+  sbim::batch_advance(b->sb);
+  for (sbim_hybrid x : b->m) ++x->n;
+}
+}  // namespace
+
+int sbim_hybrid_batch_step(sbim_hybrid_batch b) {
+  if (!b) return hfail(SBIM_ERR_ARG, "NULL batch");
+  const int rc = hbatch_enqueue(b);
+  if (rc == SBIM_OK) hbatch_advance(b);
+  return rc;
+}
+
+int sbim_hybrid_batch_capture(sbim_hybrid_batch b) {
+  if (!b) return hfail(SBIM_ERR_ARG, "NULL batch");
+  cudaStream_t st = b->m[0]->stream;
+  if (!st) return hfail(SBIM_ERR_ARG, "graph capture needs a non-default stream");
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  HCU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = hbatch_enqueue(b);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != SBIM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return hfail(SBIM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  b->graph = g;
+  HCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return SBIM_OK;
+}
+
+int sbim_hybrid_batch_replay(sbim_hybrid_batch b) {
+  if (!b) return hfail(SBIM_ERR_ARG, "NULL batch");
+  if (!b->exec) return hfail(SBIM_ERR_STATE, "no captured step: call sbim_hybrid_batch_capture");
+  HCU(cudaGraphLaunch(b->exec, b->m[0]->stream));
+  hbatch_advance(b);
+  return SBIM_OK;
+}
+
+int sbim_hybrid_batch_destroy(sbim_hybrid_batch b) {
+  if (!b) return SBIM_OK;
+  cudaStream_t st = b->m.empty() ? nullptr : b->m[0]->stream;
+  if (st) cudaStreamSynchronize(st);
+  else cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  sbim_batch_destroy(b->sb);   // the SBIM handles stay with their hybrids
+  delete b;
   return SBIM_OK;
 }
 

@@ -340,6 +340,7 @@ int create_impl(sbim_ctx* c) {
   }
 
   if (choose_chunks(*c) != SBIM_OK) return SBIM_ERR_CUDA;
+  if (c->variant >= 1) CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant));
 
   // history size
   long long rec_bytes = 0;
@@ -453,6 +454,42 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
 
 namespace sbim {
 void set_last_error(const char* msg) { g_err = msg; }
+
+StepArgs handle_step_args(sbim_handle h) { return step_args(h); }
+
+int handle_fft_forward(sbim_handle c, const void* u) {
+  if (c->prec == SBIM_FP64)
+    CF(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)u, (cufftDoubleComplex*)c->d_uhat));
+  else
+    CF(cufftExecR2C(c->plan_fwd, (cufftReal*)u, (cufftComplex*)c->d_uhat));
+  return SBIM_OK;
+}
+
+int handle_fft_inverse(sbim_handle c) {
+  if (c->prec == SBIM_FP64)
+    CF(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)c->d_s));
+  else
+    CF(cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)c->d_s));
+  return SBIM_OK;
+}
+
+int handle_epilogue(sbim_handle c, const void* v, void* tau) {
+  const double k = c->side * c->mu / c->cs;
+  const double coef[3] = {k, k * c->eta, k};
+  CU(launch_epilogue(c->prec, c->d_s, v, tau, (long long)c->n1 * c->n3, coef, c->tau_inf,
+                     c->d_step, c->stream));
+  return SBIM_OK;
+}
+
+void handle_advance(sbim_handle c) { ++c->n; }
+
+int handle_shape(sbim_handle c, int* precision, int* kahan, int* variant, void** stream) {
+  *precision = c->prec;
+  *kahan = c->kahan;
+  *variant = c->variant;
+  *stream = (void*)c->stream;
+  return SBIM_OK;
+}
 }  // namespace sbim
 
 extern "C" {
@@ -603,6 +640,14 @@ int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   const int old_v = h->variant, old_l = h->lags_per_cta, old_lc = h->lc, old_nc = h->nchunks;
   h->variant = variant;
   h->lags_per_cta = lags_per_cta;
+  if (variant >= 1) {
+    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, variant);
+    if (e != cudaSuccess) {
+      h->variant = old_v;
+      h->lags_per_cta = old_l;
+      return fail(SBIM_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    }
+  }
   int rc = choose_chunks(*h);
   if (rc == SBIM_OK) rc = alloc_partials(*h);
   if (rc != SBIM_OK) {

@@ -1,0 +1,255 @@
+// Batches of independent SBIM updates (Section 2.3) with ragged grids and
+// history lengths, advanced together: per member the two FFTs and the epilogue,
+// and ONE persistent launch of the history convolution over the (member, orbit
+// tile, lag chunk) items of all members, plus one batched assembly.  A step can
+// be captured once in a CUDA graph and replayed (the step counters live on the
+// device, so the replayed graph advances every member's history).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/sbim.h"
+#include "sbim_internal.cuh"
+
+struct sbim_batch_ctx {
+  int nb = 0, prec = SBIM_FP32, kahan = 1, shape = 2;
+  bool owns = true;
+  cudaStream_t stream = nullptr;
+  std::vector<sbim_handle> h;
+  sbim::StepArgs* d_args = nullptr;
+  int* d_item_prefix = nullptr;
+  int* d_tile_prefix = nullptr;
+  int* d_counter = nullptr;
+  int total_items = 0, total_tiles = 0, ctas = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int bfail(int code, const char* fmt, ...) {
+  char buf[400];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  sbim::set_last_error(buf);
+  return code;
+}
+
+#define BCU(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return bfail(e_ == cudaErrorMemoryAllocation ? SBIM_ERR_OOM : SBIM_ERR_CUDA,  \
+                   "%s: %s", #call, cudaGetErrorString(e_));                       \
+  } while (0)
+
+void brelease(sbim_batch_ctx* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->owns)
+    for (sbim_handle x : b->h) sbim_destroy(x);
+  void* p[] = {b->d_args, b->d_item_prefix, b->d_tile_prefix, b->d_counter};
+  for (void* x : p)
+    if (x) cudaFree(x);
+  delete b;
+}
+
+// Lag chunks of 256 lags for every member: items of comparable cost.
+constexpr int kBatchLags = 256;
+
+int setup(sbim_batch_ctx* b) {
+  int prec0 = 0, kahan0 = 0;
+  void* st0 = nullptr;
+  for (int i = 0; i < b->nb; ++i) {
+    int prec, kahan, var;
+    void* st;
+    sbim::handle_shape(b->h[i], &prec, &kahan, &var, &st);
+    (void)var;
+    if (i == 0) {
+      prec0 = prec; kahan0 = kahan; st0 = st;
+    } else if (prec != prec0 || kahan != kahan0 || st != st0) {
+      return bfail(SBIM_ERR_ARG, "batch members must share precision, compensation and stream");
+    }
+    if (prec == SBIM_FP64) return bfail(SBIM_ERR_ARG, "batches use float or bf16 history");
+  }
+  // pipeline shape of the persistent kernel: the ones that fit its register
+  // budget without spilling (float: 2 stages x 4 lags; bf16: 4 x 2 / 8 x 2)
+  const int shape = prec0 == SBIM_FP32 ? 3 : 1;
+  for (int i = 0; i < b->nb; ++i) {
+    const int rc = sbim_set_conv_config(b->h[i], shape, kBatchLags);
+    if (rc != SBIM_OK) return rc;
+  }
+  BCU(sbim::prepare_conv_tma(prec0, kahan0, shape));
+  b->prec = prec0; b->kahan = kahan0; b->shape = shape; b->stream = (cudaStream_t)st0;
+  std::vector<sbim::StepArgs> args(b->nb);
+  std::vector<int> items(b->nb + 1, 0), tiles(b->nb + 1, 0);
+  for (int i = 0; i < b->nb; ++i) {
+    args[i] = sbim::handle_step_args(b->h[i]);
+    const int t = args[i].n_orb_pad / sbim::kOrbitTile;
+    tiles[i + 1] = tiles[i] + t;
+    items[i + 1] = items[i] + t * args[i].nchunks;
+  }
+  b->total_items = items[b->nb];
+  b->total_tiles = tiles[b->nb];
+  BCU(cudaMalloc(&b->d_args, b->nb * sizeof(sbim::StepArgs)));
+  BCU(cudaMalloc(&b->d_item_prefix, (b->nb + 1) * sizeof(int)));
+  BCU(cudaMalloc(&b->d_tile_prefix, (b->nb + 1) * sizeof(int)));
+  BCU(cudaMalloc(&b->d_counter, sizeof(int)));
+  BCU(cudaMemcpyAsync(b->d_args, args.data(), b->nb * sizeof(sbim::StepArgs),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemcpyAsync(b->d_item_prefix, items.data(), (b->nb + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemcpyAsync(b->d_tile_prefix, tiles.data(), (b->nb + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  int dev = 0, sms = 148;
+  BCU(cudaGetDevice(&dev));
+  BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape);
+  return SBIM_OK;
+}
+
+// Enqueue one step of every member (pointer arrays are host arrays of device pointers).
+int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void* const* tau) {
+  for (int i = 0; i < b->nb; ++i) {
+    const int rc = sbim::handle_fft_forward(b->h[i], u[i]);
+    if (rc != SBIM_OK) return rc;
+  }
+  BCU(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
+  sbim::BatchLaunch bl;
+  bl.args = b->d_args;
+  bl.item_prefix = b->d_item_prefix;
+  bl.tile_prefix = b->d_tile_prefix;
+  bl.nb = b->nb;
+  bl.counter = b->d_counter;
+  bl.ctas = b->ctas;
+  const sbim::StepArgs a0 = sbim::handle_step_args(b->h[0]);
+  BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl));
+  BCU(sbim::launch_assemble_batch(bl, b->total_tiles, b->prec, b->kahan, b->stream));
+  for (int i = 0; i < b->nb; ++i) {
+    int rc = sbim::handle_fft_inverse(b->h[i]);
+    if (rc == SBIM_OK) rc = sbim::handle_epilogue(b->h[i], v[i], tau[i]);
+    if (rc != SBIM_OK) return rc;
+  }
+  return SBIM_OK;
+}
+
+}  // namespace
+
+namespace sbim {
+// A batch over existing handles (not owned), for drivers such as the hybrid batch.
+int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n) {
+  if (!out || !hs || n < 1) return bfail(SBIM_ERR_ARG, "bad batch arguments");
+  sbim_batch_ctx* b = new sbim_batch_ctx;
+  b->nb = n;
+  b->owns = false;
+  b->h.assign(hs, hs + n);
+  const int rc = setup(b);
+  if (rc != SBIM_OK) {
+    brelease(b);
+    return rc;
+  }
+  *out = b;
+  return SBIM_OK;
+}
+int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau) {
+  return enqueue(b, u, v, tau);
+}
+void batch_advance(sbim_batch b) {
+  for (sbim_handle x : b->h) handle_advance(x);
+}
+}  // namespace sbim
+
+extern "C" {
+
+int sbim_batch_create(sbim_batch* out, int nb, const int* n1, const int* n3, const double* L1,
+                      const double* L3, const double* cs, const double* cp, const double* rho,
+                      const double* dt, const int* n_cut, const int* side, int precision,
+                      int kahan, void* stream) {
+  if (!out || nb < 1 || !n1 || !n3 || !L1 || !L3 || !cs || !cp || !rho || !dt || !n_cut || !side)
+    return bfail(SBIM_ERR_ARG, "NULL or empty batch description");
+  if (precision == SBIM_FP64) return bfail(SBIM_ERR_ARG, "batches use float or bf16 history");
+  sbim_batch_ctx* b = new sbim_batch_ctx;
+  b->nb = nb;
+  for (int i = 0; i < nb; ++i) {
+    sbim_handle x = nullptr;
+    const int rc = sbim_create(&x, n1[i], n3[i], L1[i], L3[i], cs[i], cp[i], rho[i], dt[i],
+                               n_cut[i], side[i], precision, kahan, stream);
+    if (rc != SBIM_OK) {
+      brelease(b);
+      return rc;
+    }
+    b->h.push_back(x);
+  }
+  const int rc = setup(b);
+  if (rc != SBIM_OK) {
+    brelease(b);
+    return rc;
+  }
+  *out = b;
+  return SBIM_OK;
+}
+
+int sbim_batch_step(sbim_batch b, const void* const* u, const void* const* v, void* const* tau) {
+  if (!b || !u || !v || !tau) return bfail(SBIM_ERR_ARG, "NULL argument");
+  for (int i = 0; i < b->nb; ++i)
+    if (!u[i] || !v[i] || !tau[i]) return bfail(SBIM_ERR_ARG, "NULL field pointer (member %d)", i);
+  const int rc = enqueue(b, u, v, tau);
+  if (rc != SBIM_OK) return rc;
+  sbim::batch_advance(b);
+  return SBIM_OK;
+}
+
+int sbim_batch_capture(sbim_batch b, const void* const* u, const void* const* v, void* const* tau) {
+  if (!b || !u || !v || !tau) return bfail(SBIM_ERR_ARG, "NULL argument");
+  if (!b->stream) return bfail(SBIM_ERR_ARG, "graph capture needs a non-default stream");
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue(b, u, v, tau);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (rc != SBIM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(SBIM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  b->graph = g;
+  BCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return SBIM_OK;
+}
+
+int sbim_batch_replay(sbim_batch b) {
+  if (!b) return bfail(SBIM_ERR_ARG, "NULL batch");
+  if (!b->exec) return bfail(SBIM_ERR_STATE, "no captured step: call sbim_batch_capture first");
+  BCU(cudaGraphLaunch(b->exec, b->stream));
+  sbim::batch_advance(b);
+  return SBIM_OK;
+}
+
+int sbim_batch_member(sbim_batch b, int i, sbim_handle* h) {
+  if (!b || !h || i < 0 || i >= b->nb) return bfail(SBIM_ERR_ARG, "bad member index");
+  *h = b->h[i];
+  return SBIM_OK;
+}
+
+int sbim_batch_destroy(sbim_batch b) {
+  if (!b) return SBIM_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  brelease(b);
+  return SBIM_OK;
+}
+
+}  // extern "C"

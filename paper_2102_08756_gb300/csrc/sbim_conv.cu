@@ -105,11 +105,9 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
 }
 
 template <class S, int KAHAN>
-__global__ void __launch_bounds__(kOrbitTile) assemble_kernel(const StepArgs a) {
+__device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   using R = typename S::real;
   using C = typename S::cplx;
-  const int o = blockIdx.x * kOrbitTile + threadIdx.x;
-  if (o >= a.n_orb_pad) return;
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
   const int nch = (n_valid + a.lc - 1) / a.lc;
@@ -178,6 +176,24 @@ __global__ void __launch_bounds__(kOrbitTile) assemble_kernel(const StepArgs a) 
   if (pend >= 0) {
     fh[pend] = P1; fh[a.nbins + pend] = P2; fh[2 * (long long)a.nbins + pend] = P3;
   }
+}
+
+template <class S, int KAHAN>
+__global__ void __launch_bounds__(kOrbitTile) assemble_kernel(const StepArgs a) {
+  const int o = blockIdx.x * kOrbitTile + threadIdx.x;
+  if (o >= a.n_orb_pad) return;
+  assemble_orbit<S, KAHAN>(a, o);
+}
+
+// One CTA per orbit tile of every member of a batch.
+template <class S, int KAHAN>
+__global__ void __launch_bounds__(kOrbitTile)
+assemble_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__ tile_prefix, int nb) {
+  const int t = blockIdx.x;
+  int s = 0;
+  while (s + 1 < nb && tile_prefix[s + 1] <= t) ++s;
+  const StepArgs a = args[s];
+  assemble_orbit<S, KAHAN>(a, (t - tile_prefix[s]) * kOrbitTile + threadIdx.x);
 }
 
 template <class R>
@@ -251,6 +267,29 @@ cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStr
     case SBIM_BF16:
       return kahan ? assemble_dispatch<StoreBF16<false>, 1>(a, st)
                    : assemble_dispatch<StoreBF16<false>, 0>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class S, int KAHAN>
+cudaError_t assemble_batch_dispatch(const BatchLaunch& b, int tiles, cudaStream_t st) {
+  assemble_batch_kernel<S, KAHAN><<<tiles, kOrbitTile, 0, st>>>(b.args, b.tile_prefix, b.nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_batch(const BatchLaunch& b, int tiles, int precision, int kahan,
+                                  cudaStream_t st) {
+  switch (precision) {
+    case SBIM_FP64: return assemble_batch_dispatch<StoreF64, 0>(b, tiles, st);
+    case SBIM_FP32:
+      return kahan ? assemble_batch_dispatch<StoreF32, 1>(b, tiles, st)
+                   : assemble_batch_dispatch<StoreF32, 0>(b, tiles, st);
+    case SBIM_BF16X2:
+      return kahan ? assemble_batch_dispatch<StoreBF16<true>, 1>(b, tiles, st)
+                   : assemble_batch_dispatch<StoreBF16<true>, 0>(b, tiles, st);
+    case SBIM_BF16:
+      return kahan ? assemble_batch_dispatch<StoreBF16<false>, 1>(b, tiles, st)
+                   : assemble_batch_dispatch<StoreBF16<false>, 0>(b, tiles, st);
     default: return cudaErrorInvalidValue;
   }
 }

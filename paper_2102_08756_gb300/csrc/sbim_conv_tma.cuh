@@ -33,7 +33,7 @@ namespace tma {
 
 using namespace dev;
 
-constexpr int kWaitLimit = 1 << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;   // give up a wait after 1 s
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -48,8 +48,20 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
+__device__ const int kNoError = 0;   // drain waits after a failure ignore the flag
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `parity` to complete.  Bounded: gives up after kWaitNs
+// of wall time, or at once when the device error word is already set (another
+// CTA gave up), so a failure costs every CTA at most one second.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const int* err) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -59,8 +71,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 63u) == 63u &&
+        (global_ns() - t0 > kWaitNs || *(volatile const int*)err != 0))
+      return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
@@ -107,25 +121,29 @@ __device__ __forceinline__ void interp_nodes(const T4 nd[4], unsigned long long 
   w[3] = l0 * nd[0].w + l1 * nd[1].w + l2 * nd[2].w + l3 * nd[3].w;
 }
 
-template <class S, int KAHAN, int NS, int KS, int MINB>
-__global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepArgs a) {
+// One work item: orbit tile `tile` and lag chunk `chunk` of the update `a`.
+// The NS mbarriers of `full` are initialised once per CTA; their phases carry
+// over from item to item through the running stage count `gstage` (stage s of
+// this item is global stage gstage + s: buffer (gstage + s) % NS, parity
+// ((gstage + s) / NS) & 1).  Returns false if a bounded wait gave up.
+template <class S, int KAHAN, int NS, int KS>
+__device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int chunk,
+                                              unsigned char* smem, unsigned long long* full,
+                                              unsigned& gstage) {
   using R = typename S::real;
   using C = typename S::cplx;
   using T4 = typename S::tab4;
   constexpr int SEG = seg_bytes<S>();
   constexpr int STAGE = stage_bytes<S, KS>();
   constexpr int MPC = S::kChunkMembers, NCH = S::kChunks;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long full[NS];
 
   const int tid = threadIdx.x;
-  const int tile0 = blockIdx.x * kOrbitTile;
+  const int tile0 = tile * kOrbitTile;
   const int o = tile0 + tid;
-  const int chunk = blockIdx.y;
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
   const int m0 = chunk * a.lc;
-  if (m0 >= n_valid) return;   // uniform over the CTA
+  if (m0 >= n_valid) return true;   // uniform over the CTA
   const int m1 = min(m0 + a.lc, n_valid);
   const int sn = (int)(n % a.n_cut);
   const R dT = reinterpret_cast<const R*>(a.dT)[o];
@@ -170,16 +188,10 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
 
   const int nst = (m1 - mf + KS - 1) / KS;
   if (nst > 0) {
-    if (tid == 0) {
-#pragma unroll
-      for (int b = 0; b < NS; ++b) mbar_init(smem_addr(&full[b]), 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
     const unsigned char* hist = reinterpret_cast<const unsigned char*>(a.hist);
     const long long plane_bytes = a.slot_stride * S::kRecBytes;
     auto issue = [&](int s) {
-      const int b = s % NS;
+      const int b = (int)((gstage + s) % NS);
       const int mb = mf + s * KS;
       const int kk = min(KS, m1 - mb);
       const unsigned bar = smem_addr(&full[b]);
@@ -223,7 +235,8 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
     for (int i = 0; i < nst; ++i) {
       // The CTA-wide vote makes the give-up decision uniform and certifies that
       // every thread has finished stage i-1, whose buffer is refilled next.
-      const bool landed = mbar_wait(smem_addr(&full[i % NS]), (unsigned)((i / NS) & 1));
+      const unsigned gi = gstage + i;
+      const bool landed = mbar_wait(smem_addr(&full[gi % NS]), (gi / NS) & 1u, a.err);
       if (!__syncthreads_and(landed)) {
         ok = false;
         break;
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
       for (int k = 0; k < KS; ++k)
         if (mn + k < m1) fetch_nodes(tab, (unsigned long long)(mn + k) * us, nd[k]);
 
-      const unsigned char* stage = smem + (i % NS) * STAGE;
+      const unsigned char* stage = smem + (gi % NS) * STAGE;
 #pragma unroll
       for (int r = 0; r < NCH; ++r) {
         const int ch = (r + rot) % NCH;
@@ -300,10 +313,13 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
       if (tid == 0) atomicExch(a.err, 1);
       // let the copies still in flight land before the CTA's shared memory is released
       const int issued = min(nst, done + NS - 1);
-      for (int s = done; s < issued; ++s)
-        mbar_wait(smem_addr(&full[s % NS]), (unsigned)((s / NS) & 1));
-      return;
+      for (int s = done; s < issued; ++s) {
+        const unsigned gs = gstage + s;
+        mbar_wait(smem_addr(&full[gs % NS]), (gs / NS) & 1u, &kNoError);
+      }
+      return false;
     }
+    gstage += nst;
   }
 
   R* part = reinterpret_cast<R*>(a.part);
@@ -315,21 +331,99 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
       part[((long long)chunk * (4 * kFields) + member * kFields + k) * orb + o] =
           KAHAN ? acc[g][k] - cmp[g][k] : acc[g][k];
   }
+  return true;
+}
+
+template <int NS>
+__device__ __forceinline__ void init_barriers(unsigned long long* full) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int b = 0; b < NS; ++b) mbar_init(smem_addr(&full[b]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// One CTA per (orbit tile, lag chunk) of one update.
+template <class S, int KAHAN, int NS, int KS, int MINB>
+__global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[NS];
+  init_barriers<NS>(full);
+  unsigned gstage = 0;
+  conv_tma_item<S, KAHAN, NS, KS>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
+}
+
+// Persistent CTAs over the (update, tile, chunk) items of a batch of updates
+// with ragged grids and history lengths: items are taken from *counter in
+// order (item_prefix[s] .. item_prefix[s+1]-1 belong to update s, tile-major
+// within each lag chunk).  Every item writes its own partial sums, so the
+// result does not depend on which CTA ran it.
+template <class S, int KAHAN, int NS, int KS, int MINB>
+__global__ void __launch_bounds__(kOrbitTile, MINB)
+conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
+                      int nb, int* counter) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[NS];
+  __shared__ int s_item, s_tile, s_chunk;
+  __shared__ StepArgs s_args;   // the item's update, read from shared memory (no registers)
+  init_barriers<NS>(full);
+  unsigned gstage = 0;
+  const int total = item_prefix[nb];
+  for (;;) {
+    __syncthreads();   // the previous item's buffers and arguments are free
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(counter, 1);
+      s_item = it;
+      if (it < total) {
+        int s = 0;
+        while (s + 1 < nb && item_prefix[s + 1] <= it) ++s;
+        s_args = args[s];
+        const int tiles = s_args.n_orb_pad / kOrbitTile;
+        const int local = it - item_prefix[s];
+        s_tile = local % tiles;
+        s_chunk = local / tiles;
+      }
+    }
+    __syncthreads();
+    if (s_item >= total) break;
+    if (!conv_tma_item<S, KAHAN, NS, KS>(s_args, s_tile, s_chunk, smem, full, gstage)) return;
+  }
 }
 
 // Launch one instantiation (sets the dynamic shared-memory attribute once).
+// With `batch` set, launches the persistent kernel over the batch's items on
+// `batch->ctas` CTAs instead.
 template <class S, int KAHAN, int NS, int KS, int MINB>
-cudaError_t launch_shape(const StepArgs& a, cudaStream_t st) {
+cudaError_t prepare_shape() {
   static bool attr_set = false;
   constexpr int bytes = smem_bytes<S, NS, KS>();
   if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
-  conv_tma_kernel<S, KAHAN, NS, KS, MINB><<<grid, kOrbitTile, bytes, st>>>(a);
+  return cudaSuccess;
+}
+
+// With `batch` null and `prepare_only` set, only sets the kernels' attributes.
+template <class S, int KAHAN, int NS, int KS, int MINB>
+cudaError_t launch_shape(const StepArgs& a, cudaStream_t st, const BatchLaunch* batch = nullptr,
+                         bool prepare_only = false) {
+  constexpr int bytes = smem_bytes<S, NS, KS>();
+  const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB>();
+  if (pe != cudaSuccess || prepare_only) return pe;
+  if (batch) {
+    conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB><<<batch->ctas, kOrbitTile, bytes, st>>>(
+        batch->args, batch->item_prefix, batch->nb, batch->counter);
+  } else {
+    const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
+    conv_tma_kernel<S, KAHAN, NS, KS, MINB><<<grid, kOrbitTile, bytes, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

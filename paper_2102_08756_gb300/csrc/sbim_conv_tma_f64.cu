@@ -5,12 +5,13 @@
 
 namespace sbim {
 
-cudaError_t launch_conv_tma_f64(const StepArgs& a, int /*kahan*/, int shape, cudaStream_t st) {
+cudaError_t launch_conv_tma_f64(const StepArgs& a, int /*kahan*/, int shape, cudaStream_t st,
+                                 const BatchLaunch* batch, bool prep) {
   using S = dev::StoreF64;
   switch (shape) {
-    case 1: return tma::launch_shape<S, 0, 3, 1, 2>(a, st);
-    case 2: return tma::launch_shape<S, 0, 4, 1, 2>(a, st);
-    case 3: return tma::launch_shape<S, 0, 2, 2, 2>(a, st);
+    case 1: return tma::launch_shape<S, 0, 3, 1, 2>(a, st, batch, prep);
+    case 2: return tma::launch_shape<S, 0, 4, 1, 2>(a, st, batch, prep);
+    case 3: return tma::launch_shape<S, 0, 2, 2, 2>(a, st, batch, prep);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/sbim.h"
+
 namespace sbim {
 
 constexpr int kMembers = 4;      // members per orbit
@@ -52,14 +54,29 @@ struct StepArgs {
   long long slot_stride;           // elements of one history plane (BF16X2 lo offset)
 };
 
+// Persistent launch over the (update, tile, chunk) items of a batch.
+struct BatchLaunch {
+  const StepArgs* args;     // [nb] device copies of the members' StepArgs
+  const int* item_prefix;   // [nb + 1] first item of each member (tiles x chunks each)
+  const int* tile_prefix;   // [nb + 1] first tile of each member (assembly grid)
+  int nb;
+  int* counter;             // work counter, zero before each launch
+  int ctas;                 // persistent CTAs
+};
+
 cudaError_t launch_conv(const StepArgs& a, int precision, int kahan, cudaStream_t s);
+cudaError_t launch_assemble_batch(const BatchLaunch& b, int total_tiles, int precision, int kahan,
+                                  cudaStream_t s);
 // History convolution with TMA bulk-copy staging of the history slots in shared
 // memory (same inputs and outputs as launch_conv).  ctas_per_sm reports the
 // residency the launch is sized for.
 // shape 1..3 selects the pipeline (stages, lags per stage, CTAs per SM).
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t s);
+                            cudaStream_t s, const BatchLaunch* batch = nullptr);
 int conv_tma_ctas_per_sm(int precision, int shape);
+// Set the shared-memory attributes of a shape's kernels (done before any launch,
+// so that launches can be captured in a CUDA graph).
+cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
                             long long plane, const double coef[3], const double tau_inf[3],
@@ -77,5 +94,19 @@ cudaError_t launch_table_build(double* out64, float* out32, long long n, double 
 
 // Set the calling thread's message returned by sbim_last_error().
 void set_last_error(const char* msg);
+
+// Stages of one handle's update, for drivers that batch the convolution of
+// several handles (each returns an sbim_status).
+StepArgs handle_step_args(sbim_handle h);
+int handle_fft_forward(sbim_handle h, const void* u);
+int handle_fft_inverse(sbim_handle h);
+int handle_epilogue(sbim_handle h, const void* v, void* tau);
+void handle_advance(sbim_handle h);
+int handle_shape(sbim_handle h, int* precision, int* kahan, int* variant, void** stream);
+
+// Batch over existing handles (not owned); enqueue one step / advance the counters.
+int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n);
+int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
+void batch_advance(sbim_batch b);
 
 }  // namespace sbim

@@ -60,6 +60,16 @@ def lib():
     L.sbim_hybrid_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ll),
                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.sbim_hybrid_destroy.argtypes = [vp]
+    L.sbim_batch_create.argtypes = [ctypes.POINTER(vp), i] + [vp] * 11 + [i, i, vp]
+    L.sbim_batch_step.argtypes = [vp, vp, vp, vp]
+    L.sbim_batch_capture.argtypes = [vp, vp, vp, vp]
+    L.sbim_batch_replay.argtypes = [vp]
+    L.sbim_batch_member.argtypes = [vp, i, ctypes.POINTER(vp)]
+    L.sbim_batch_destroy.argtypes = [vp]
+    L.sbim_hybrid_batch_create.argtypes = [ctypes.POINTER(vp), i, vp]
+    for nm in ("sbim_hybrid_batch_step", "sbim_hybrid_batch_capture", "sbim_hybrid_batch_replay",
+               "sbim_hybrid_batch_destroy"):
+        getattr(L, nm).argtypes = [vp]
     L.sbim_last_error.argtypes = []
     L.sbim_last_error.restype = ctypes.c_char_p
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
@@ -69,7 +79,11 @@ def lib():
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
                  "sbim_hybrid_step", "sbim_hybrid_fault_fields", "sbim_hybrid_info",
-                 "sbim_hybrid_destroy"):
+                 "sbim_hybrid_destroy", "sbim_batch_create", "sbim_batch_step",
+                 "sbim_batch_capture", "sbim_batch_replay", "sbim_batch_member",
+                 "sbim_batch_destroy", "sbim_hybrid_batch_create", "sbim_hybrid_batch_step",
+                 "sbim_hybrid_batch_capture", "sbim_hybrid_batch_replay",
+                 "sbim_hybrid_batch_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -154,6 +168,69 @@ def sbim_destroy(h):
 
 def sbim_last_error():
     return lib().sbim_last_error().decode()
+
+
+def _ptrs(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+
+def sbim_batch_create(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, precision, kahan, stream):
+    """Per-member sequences of equal length nb."""
+    import numpy as np
+    nb = len(n1)
+    ints = [np.ascontiguousarray(x, dtype=np.int32) for x in (n1, n3, n_cut, side)]
+    dbls = [np.ascontiguousarray(x, dtype=np.float64) for x in (L1, L3, cs, cp, rho, dt)]
+    b = ctypes.c_void_p()
+    _check(lib().sbim_batch_create(ctypes.byref(b), nb, ints[0].ctypes.data, ints[1].ctypes.data,
+                                   *[d.ctypes.data for d in dbls], ints[2].ctypes.data,
+                                   ints[3].ctypes.data, precision, kahan, stream))
+    return b
+
+
+def sbim_batch_step(b, u_ptrs, v_ptrs, tau_ptrs):
+    _check(lib().sbim_batch_step(b, _ptrs(u_ptrs), _ptrs(v_ptrs), _ptrs(tau_ptrs)))
+
+
+def sbim_batch_capture(b, u_ptrs, v_ptrs, tau_ptrs):
+    _check(lib().sbim_batch_capture(b, _ptrs(u_ptrs), _ptrs(v_ptrs), _ptrs(tau_ptrs)))
+
+
+def sbim_batch_replay(b):
+    _check(lib().sbim_batch_replay(b))
+
+
+def sbim_batch_member(b, i):
+    h = ctypes.c_void_p()
+    _check(lib().sbim_batch_member(b, i, ctypes.byref(h)))
+    return h
+
+
+def sbim_batch_destroy(b):
+    _check(lib().sbim_batch_destroy(b))
+
+
+def sbim_hybrid_batch_create(members):
+    b = ctypes.c_void_p()
+    _check(lib().sbim_hybrid_batch_create(ctypes.byref(b), len(members),
+                                          _ptrs([m.value if hasattr(m, "value") else m
+                                                 for m in members])))
+    return b
+
+
+def sbim_hybrid_batch_step(b):
+    _check(lib().sbim_hybrid_batch_step(b))
+
+
+def sbim_hybrid_batch_capture(b):
+    _check(lib().sbim_hybrid_batch_capture(b))
+
+
+def sbim_hybrid_batch_replay(b):
+    _check(lib().sbim_hybrid_batch_replay(b))
+
+
+def sbim_hybrid_batch_destroy(b):
+    _check(lib().sbim_hybrid_batch_destroy(b))
 
 
 def sbim_hybrid_create(n1, n2, n3, h, cs, cp, rho, dt, n_cut, precision, boundaries, fault,
