@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--variant", type=int, default=-1,
                    help="convolution kernel: -1 library default, 1-3 TMA-staged shapes, 0 register prefetch")
     p.add_argument("--lags-per-cta", type=int, default=0)
+    p.add_argument("--window", type=float, default=0.0,
+                   help="mode-dependent truncation window in T = |k| c_s t (0: uniform cutoff)")
     p.add_argument("--tune", action="store_true",
                    help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
@@ -81,6 +83,21 @@ def workload_name(c, precision, kahan):
 
 def n_modes(c):
     return c["n3"] * (c["n1"] // 2 + 1)
+
+
+def lag_pairs(c, window):
+    """Mode-lag pairs of one full-history step: n_modes x n_cut, or with a
+    truncation window the sum over modes of min(n_cut, floor(window/dT) + 1)."""
+    if window <= 0:
+        return n_modes(c) * c["n_cut"]
+    j1 = np.arange(c["n1"] // 2 + 1)[None, :]
+    r3 = np.arange(c["n3"])[:, None]
+    j3 = np.where(r3 <= c["n3"] // 2, r3, r3 - c["n3"])
+    q = np.hypot(2 * np.pi * j1 / c["L1"], 2 * np.pi * j3 / c["L3"])
+    dT = q * c["cs"] * c["dt"]
+    lim = np.where(dT > 0, np.minimum(np.floor(window / np.where(dT > 0, dT, 1)) + 1, c["n_cut"]),
+                   c["n_cut"])
+    return int(lim.sum())
 
 
 def peaks():
@@ -154,6 +171,23 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, device=None):
+    """The maximum of a per-rank float over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_per_rank, world):
+    """Whole-job throughput of ``world`` replicas: all units over the slowest
+    rank's time (weak scaling: every rank processes ``units_per_rank``)."""
+    return world * units_per_rank / seconds_per_rank
 
 
 def dist_setup(args):
@@ -251,6 +285,8 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     g = SBIM(n1, n3, c["L1"], c["L3"], c["cs"], c["cp"], c["rho"], dt, n_cut, 1, prec,
              bool(args.kahan), stream=stream)
+    if args.window > 0:
+        g.set_window(args.window)
     if args.variant >= 0 or args.lags_per_cta:
         g.set_conv_config(args.variant if args.variant >= 0 else DEFAULT_VARIANT[prec],
                           args.lags_per_cta)
@@ -314,25 +350,22 @@ def run_native(args):
     g.set_profiling(False)
     g.check()
     hist_bytes = g.info()["hist_bytes"]
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     ms_step = ms_total / K
     modes = n_modes(c)
-    L = n_cut
-    macs_step = modes * L * MACS_PER_PAIR
-    value = world * macs_step / (ms_step * 1e-3)
+    pairs = lag_pairs(c, args.window)
+    macs_step = pairs * MACS_PER_PAIR
+    value = job_throughput(macs_step, ms_step * 1e-3, world)
 
     # roofline of the convolution kernel (algorithmic bytes per launch)
     conv_ms = stage["convolution"] / nprof
     bpp = BYTES_PER_PAIR[prec]
-    alg_bytes = modes * (L + 1) * bpp
+    alg_bytes = (pairs + modes) * bpp
     achieved = alg_bytes / (conv_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     traffic = None
     if NCU_TRAFFIC["conv_src_sha1"] == conv_src_sha1() and prec == "fp32" and n1 == 1024 \
-            and args.variant in (-1, 2) and not args.lags_per_cta \
+            and args.variant in (-1, 2) and not args.lags_per_cta and args.window <= 0 \
             and n_cut == 4096:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
 
@@ -355,12 +388,9 @@ def run_native(args):
             B.sbim_step_host(g.h, hu.data_ptr(), hv.data_ptr(), ht.data_ptr())
         t1 = time.perf_counter()
         e2e_s = (t1 - t0) / K
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dev)
         fb = hu.numel() * hu.element_size()
-        e2e = {"value": world * macs_step / e2e_s, "unit": "MAC/s",
+        e2e = {"value": job_throughput(macs_step, e2e_s, world), "unit": "MAC/s",
                "h2d_bytes_per_step": 2 * fb, "d2h_bytes_per_step": fb,
                "ms_per_step": e2e_s * 1e3}
     g.close()
@@ -384,6 +414,7 @@ def run_native(args):
         "config": {"workload": workload_name(c, prec, args.kahan), "n1": n1, "n3": n3,
                    "n_cut": n_cut, "precision": prec, "kahan": int(bool(args.kahan)),
                    "conv_variant": args.variant if args.variant >= 0 else DEFAULT_VARIANT[prec],
+                   "window": args.window, "mode_lag_pairs": pairs,
                    "modes": modes, "history_bytes": hist_bytes,
                    "l2": "inputs larger than L2 (history ring buffer >> 129 MB)",
                    "parallelism": f"replicas x{world}"},

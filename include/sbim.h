@@ -178,6 +178,17 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
 int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta);
 
 /*
+ * sbim_set_window -- mode-dependent truncation of the convolution (the paper cites
+ * the truncation of Lapusta et al. without giving a rule): a window fixed in the
+ * dimensionless time T = |k| c_s t, so mode k keeps its lags m with
+ * m |k| c_s dt <= window (at most n_cut; k = 0 keeps n_cut).  Long-wavelength modes
+ * keep long histories, short ones short: the bytes read per step drop with the
+ * window.  window = 0 restores the uniform cutoff.  The ring buffer keeps n_cut
+ * slots either way.  Takes effect for the following steps.
+ */
+int sbim_set_window(sbim_handle h, double window);
+
+/*
  * sbim_check_device -- wait for the handle's stream and report whether any
  * bounded device-side wait of the convolution gave up since the last check
  * (SBIM_ERR_TIMEOUT; the tractions computed since then are invalid).  Clears the

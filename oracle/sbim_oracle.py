@@ -392,6 +392,15 @@ def apply_modal_operator(modes, mat, side, weights, hist_rev, current):
     return F
 
 
+def lag_limits(dT, n_cut, window):
+    """Lags kept per mode under a truncation window in T: floor(window/dT) + 1,
+    at most n_cut (all n_cut for k = 0)."""
+    dT = np.asarray(dT, dtype=float)
+    safe = np.where(dT > 0, dT, 1.0)
+    lim = np.floor(window / safe) + 1
+    return np.where(dT > 0, np.minimum(lim, n_cut), n_cut).astype(np.int64)
+
+
 class SBIMOracle:
     """Time stepper of Eq. (SBI) for one half-space on a periodic N1 x N3 grid.
 
@@ -402,7 +411,7 @@ class SBIMOracle:
     """
 
     def __init__(self, n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side,
-                 tau_inf=(0.0, 0.0, 0.0), kernel="table"):
+                 tau_inf=(0.0, 0.0, 0.0), kernel="table", window=0.0):
         if n1 % 2 or n3 % 2 or n1 < 2 or n3 < 2:
             raise ValueError("n1, n3 must be even and >= 2")
         if side not in (1, -1):
@@ -426,6 +435,15 @@ class SBIMOracle:
         uniq, inv = np.unique(self.dT, return_inverse=True)
         wu = np.stack([trapezoid_weights(d, n_cut, kern) for d in uniq], axis=1)
         self.weights = wu[:, inv, :]             # (4, nmodes, n_cut)
+        if window > 0:
+            # mode-dependent truncation (the convolution truncation the paper cites
+            # from Lapusta et al.): mode q keeps the lags with m dT_q <= window,
+            # i.e. a window fixed in T = |k| c_s t, so a fixed number of periods
+            self.lags = lag_limits(self.dT, n_cut, window)
+            m = np.arange(n_cut)[None, :]
+            self.weights = self.weights * (m < self.lags[:, None])[None]
+        else:
+            self.lags = np.full(self.dT.shape, n_cut)
         self.history = []                         # list of (3, nmodes) complex
         self.n = 0
 

@@ -130,6 +130,10 @@ struct sbim_ctx {
   void* d_s = nullptr;
   long long* d_step = nullptr;
   int* d_err = nullptr;
+  int* d_lmax = nullptr;
+  int* d_tile_lmax = nullptr;
+  double window = 0.0;
+  std::vector<double> h_dT;   // |k| c_s dt per orbit (host copy)
   void* d_io = nullptr;  // u, v, tau staging for sbim_step_host
   cufftHandle plan_fwd = 0, plan_inv = 0;
   bool have_fwd = false, have_inv = false;
@@ -274,7 +278,8 @@ void release(sbim_ctx* c) {
   if (c->have_inv) cufftDestroy(c->plan_inv);
   void* ptrs[] = {c->d_bin, c->d_dir, c->d_wout, c->d_dT, c->d_ustep, c->d_muq,
                   c->d_tab64, c->d_tab32, c->d_gl, c->d_hist, c->d_part, c->d_uhat,
-                  c->d_fhat, c->d_s, c->d_step, c->d_err, c->d_io};
+                  c->d_fhat, c->d_s, c->d_step, c->d_err, c->d_io, c->d_lmax,
+                  c->d_tile_lmax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -322,6 +327,7 @@ int create_impl(sbim_ctx* c) {
     dT_max = std::max(dT_max, dT[o]);
     ustep[o] = (unsigned long long)std::llround(dT[o] / c->tab_h * 4294967296.0);
   }
+  c->h_dT = dT;
   const double t_max = dT_max * (c->n_cut - 1);
   c->tab_n = (long long)std::floor(t_max / c->tab_h) + 6;  // nodes -1 .. floor + 4
   if ((double)c->n_cut * (dT_max / c->tab_h + 1.0) * 4294967296.0 > 1.8e19 ||
@@ -432,6 +438,8 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
   a.ustep = c->d_ustep;
   a.muq = c->d_muq;
   a.table = c->prec == SBIM_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
+  a.lmax = c->window > 0 ? c->d_lmax : nullptr;
+  a.tile_lmax = c->window > 0 ? c->d_tile_lmax : nullptr;
   a.hist = c->d_hist;
   a.step = c->d_step;
   a.err = c->d_err;
@@ -618,6 +626,32 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
   CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return sbim_check_device(h);
+}
+
+int sbim_set_window(sbim_handle h, double window) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!(window >= 0)) return fail(SBIM_ERR_ARG, "window must be >= 0");
+  if (window == 0) {
+    h->window = 0;
+    return SBIM_OK;
+  }
+  std::vector<int> lm(h->n_orb_pad), tl(h->n_orb_pad / sbim::kOrbitTile, 1);
+  for (int o = 0; o < h->n_orb_pad; ++o) {
+    const double d = h->h_dT[o];
+    if (o >= h->n_orb) lm[o] = 1;                       // padding orbits
+    else if (d <= 0) lm[o] = h->n_cut;                  // k = 0
+    else lm[o] = (int)std::min<double>(h->n_cut, std::floor(window / d) + 1);
+    int& t = tl[o / sbim::kOrbitTile];
+    t = std::max(t, lm[o]);
+  }
+  if (!h->d_lmax) CU(cudaMalloc(&h->d_lmax, lm.size() * sizeof(int)));
+  if (!h->d_tile_lmax) CU(cudaMalloc(&h->d_tile_lmax, tl.size() * sizeof(int)));
+  CU(cudaMemcpyAsync(h->d_lmax, lm.data(), lm.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->d_tile_lmax, tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->window = window;
+  return SBIM_OK;
 }
 
 int sbim_check_device(sbim_handle h) {

@@ -42,8 +42,10 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
   const int m0 = chunk * a.lc;
-  if (m0 >= n_valid) return;
-  const int m1 = min(m0 + a.lc, n_valid);
+  const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[blockIdx.x]) : n_valid;
+  if (m0 >= m_end) return;
+  const int m1 = min(m0 + a.lc, m_end);
+  const int lo = a.lmax ? a.lmax[o] : 0x7fffffff;   // this orbit's truncation
   const int sn = (int)(n % a.n_cut);
   const R dT = reinterpret_cast<const R*>(a.dT)[o];
   const unsigned long long us = a.ustep[o];
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
         for (int c = 0; c < 3; ++c) S::load(a.hist, ((long long)slot * 3 + c) * orb + o, plane, Dn[c]);
       }
       R w[4];
-      lag_weights(tab, u, dT, w);
+      lag_weights(tab, u, m < lo ? dT : (R)0, w);
       u += us;
       accumulate<KAHAN>(acc, cmp, w, D);
     }
@@ -110,7 +112,8 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   using C = typename S::cplx;
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
-  const int nch = (n_valid + a.lc - 1) / a.lc;
+  const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[o / kOrbitTile]) : n_valid;
+  const int nch = (m_end + a.lc - 1) / a.lc;
   const long long orb = a.n_orb_pad;
   const R muq = reinterpret_cast<const R*>(a.muq)[o];
   const R sd = (R)a.side;

@@ -143,8 +143,10 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
   const int m0 = chunk * a.lc;
-  if (m0 >= n_valid) return true;   // uniform over the CTA
-  const int m1 = min(m0 + a.lc, n_valid);
+  const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[tile]) : n_valid;
+  if (m0 >= m_end) return true;   // uniform over the CTA
+  const int m1 = min(m0 + a.lc, m_end);
+  const int lo = a.lmax ? a.lmax[o] : 0x7fffffff;   // this orbit's truncation
   const int sn = (int)(n % a.n_cut);
   const R dT = reinterpret_cast<const R*>(a.dT)[o];
   const unsigned long long us = a.ustep[o];
@@ -222,7 +224,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
         if (mf + k < m1) fetch_nodes(tab, (unsigned long long)(mf + k) * us, nd[k]);
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
-        if (mf + k < m1) {
+        if (mf + k < m1 && mf + k < lo) {
           interp_nodes(nd[k], (unsigned long long)(mf + k) * us, dT, wn[k]);
         } else {
           wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
@@ -302,7 +304,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       }
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
-        if (mn + k < m1) {
+        if (mn + k < m1 && mn + k < lo) {
           interp_nodes(nd[k], (unsigned long long)(mn + k) * us, dT, wn[k]);
         } else {
           wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;

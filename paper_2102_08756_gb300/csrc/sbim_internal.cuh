@@ -35,6 +35,8 @@ struct StepArgs {
   const unsigned long long* ustep; // [n_orb_pad] dT / h in 32.32 fixed point
   const void* muq;                 // [n_orb_pad] mu |k| (float or double)
   const void* table;               // [table_n] (H11, H22, H33, H12) at T = (j-1) h
+  const int* lmax;                 // [n_orb_pad] lags kept per orbit (truncation window), or NULL
+  const int* tile_lmax;            // [n_orb_pad/128] max of lmax over each tile, or NULL
   // state
   void* hist;                      // ring buffer (layout per precision)
   long long* step;                 // device step counter n

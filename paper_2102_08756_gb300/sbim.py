@@ -48,6 +48,7 @@ def lib():
     L.sbim_set_profiling.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
     L.sbim_set_conv_config.argtypes = [vp, i, i]
+    L.sbim_set_window.argtypes = [vp, d]
     L.sbim_check_device.argtypes = [vp]
     L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
@@ -60,7 +61,7 @@ def lib():
     L.sbim_hybrid_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ll),
                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.sbim_hybrid_destroy.argtypes = [vp]
-    L.sbim_batch_create.argtypes = [ctypes.POINTER(vp), i] + [vp] * 11 + [i, i, vp]
+    L.sbim_batch_create.argtypes = [ctypes.POINTER(vp), i] + [vp] * 10 + [i, i, vp]
     L.sbim_batch_step.argtypes = [vp, vp, vp, vp]
     L.sbim_batch_capture.argtypes = [vp, vp, vp, vp]
     L.sbim_batch_replay.argtypes = [vp]
@@ -75,7 +76,7 @@ def lib():
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
                  "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
-                 "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device",
+                 "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device", "sbim_set_window",
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
                  "sbim_hybrid_step", "sbim_hybrid_fault_fields", "sbim_hybrid_info",
@@ -148,6 +149,10 @@ def sbim_stage_times(h):
 
 def sbim_set_conv_config(h, variant, lags_per_cta=0):
     _check(lib().sbim_set_conv_config(h, int(variant), int(lags_per_cta)))
+
+
+def sbim_set_window(h, window):
+    _check(lib().sbim_set_window(h, float(window)))
 
 
 def sbim_check_device(h):
@@ -356,6 +361,10 @@ class SBIM:
 
     def set_conv_config(self, variant, lags_per_cta=0):
         sbim_set_conv_config(self.h, variant, lags_per_cta)
+
+    def set_window(self, window):
+        """Mode-dependent truncation window in T = |k| c_s t (0: uniform cutoff)."""
+        sbim_set_window(self.h, window)
 
     def check(self):
         """Wait for the stream; raise if a bounded device wait gave up."""

@@ -233,3 +233,43 @@ def test_large_boundary_sampled_modes(precision, kahan, tol, variant):
     got = F_gpu[:, r3, j1]
     err = max(np.linalg.norm(got[k] - F_ref[k]) / np.linalg.norm(F_ref[k]) for k in range(3))
     assert err < tol, err
+
+
+def _window_avoiding_integers(dT, window):
+    """Nudge the window so no mode's window/dT sits within 1e-6 of an integer
+    (the kept-lag count must not hinge on the last bit of dT)."""
+    w = window
+    for _ in range(100):
+        r = w / dT[dT > 0]
+        if np.all(np.abs(r - np.round(r)) > 1e-6):
+            return w
+        w *= 1.0 + 1e-4
+    return w
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("grid,window", [((16, 16, 1600.0, 1600.0), 4.0), ((8, 6, 800.0, 900.0), 9.0)])
+def test_truncation_window_matches_oracle(variant, grid, window):
+    """Mode-dependent truncation: every mode keeps the lags with m dT <= window."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    n1, n3, L1, L3 = grid
+    n_cut, steps, side = 40, 50, -1
+    dt = 0.3 * (L1 / n1) / CP
+    o = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
+    window = _window_avoiding_integers(o.dT, window)
+    o = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, window=window)
+    assert o.lags.min() < n_cut and o.lags[o.dT > 0].max() > 1
+    g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, "fp32", True)
+    g.set_conv_config(variant)
+    g.set_window(window)
+    hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=31, spectrum="k2")
+    zero = torch.zeros((3, n3, n1), device="cuda")
+    worst = 0.0
+    for m in range(steps):
+        u = hist.u(m).astype(np.float32)
+        s = g.step(torch.from_numpy(u).cuda(), zero).double().cpu().numpy()
+        r = o.step(u.astype(np.float64), np.zeros((3, n3, n1)))["s"]
+        if np.linalg.norm(r) > 0:
+            worst = max(worst, rel_l2(s, r))
+    g.check()
+    assert worst < 1e-5, worst

@@ -161,3 +161,25 @@ def test_nyquist_content_gives_real_output():
     for _ in range(6):
         out = o.step(rng.normal(size=(3, 6, n)) * 1e-3, rng.normal(size=(3, 6, n)))
         assert out["imag"] < 1e-12 * np.max(np.abs(out["s"]))
+
+
+def test_truncation_window_keeps_the_early_lags():
+    """A window of 3 (in T) keeps the lags with m dT <= 3: the antiplane
+    impulse response is the untruncated one up to there and zero after."""
+    n, dx = 8, 100.0
+    full = _oracle(n=n, n_cut=64)
+    cut = SBIMOracle(n, n, n * dx, n * dx, CS, CP, RHO, 0.3 * dx / CP, 64, 1, window=3.0)
+    k1 = 2 * np.pi / (n * dx)
+    dT = k1 * CS * full.dt
+    keep = int(np.floor(3.0 / dT)) + 1
+    pat = np.cos(k1 * np.arange(n) * dx)[None, :] * np.ones((n, 1))
+    for m in range(keep + 5):
+        u = np.zeros((3, n, n))
+        if m == 0:
+            u[2] = pat
+        a = full.step(u, np.zeros_like(u))["s"][2]
+        b = cut.step(u, np.zeros_like(u))["s"][2]
+        if m < keep:
+            np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.max(np.abs(a)))
+        else:
+            assert np.max(np.abs(b)) < 1e-9 * np.max(np.abs(a)) + 1e-300
