@@ -38,7 +38,7 @@ DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 3, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"conv_src_sha1": "7ebcc73cd57143cff62d6a79996ddfe96205df72", "bytes_per_launch": 52.16e9 + 183.56e6}
+NCU_TRAFFIC = {"conv_src_sha1": "f48c0cd7a90671a809a89162abd5b5e973127271", "bytes_per_launch": 52.16e9 + 183.99e6}
 
 
 def parse():
@@ -58,7 +58,7 @@ def parse():
                    help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
-    p.add_argument("--workload", default="sbim", choices=["sbim", "coupled", "ensemble"],
+    p.add_argument("--workload", default="sbim", choices=["sbim", "coupled", "ensemble", "adjoint"],
                    help="sbim: the single half-space update (default); coupled: FEM slab + fault "
                         "between two half-spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -573,6 +573,73 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Gradient of a squared fault-traction misfit J = 1/2 sum_n |tau_n - tau*_n|^2
+    (seeded target) with respect to Dc through 500 coupled steps: 256 x 8 x 256
+    hex slab (dx = 100 m) with a slip-weakening fault between two SBIM half-spaces,
+    1024-lag FP32 histories, FE checkpoints every 50 steps; plus the misfit's
+    gradient with respect to a 500-step boundary displacement history through
+    the SBIM-only update (autograd over sbim_step / sbim_step_adjoint)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2102_08756_gb300 import _build
+    _build.build()
+    from paper_2102_08756_gb300.autograd import hybrid_rupture, sbim_sequence
+    n = args.n or 256
+    steps = args.steps if args.steps != 200 else 500
+    h, cs, cp, rho = 100.0, 3464.0, 6000.0, 2670.0
+    dt = 0.3 * h / cp
+    c = (np.arange(n) - n / 2 + 0.5) * h
+    X3, X1 = np.meshgrid(c, c, indexing="ij")
+    patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
+    tau0 = np.where(patch, 1.005 * 0.677 * 120e6, 70e6)
+    kw = dict(n1=n, n2=8, n3=n, h=h, cs=cs, cp=cp, rho=rho, dt=dt, n_cut=args.n_cut or 1024,
+              mu_s=np.full((n, n), 0.677), tau0=tau0, mu_k=0.525, sigma0=120e6, steps=steps,
+              every=50)
+    gen = torch.Generator(device="cuda").manual_seed(5000)
+    target = torch.randn((steps, 3, n, n), device="cuda", generator=gen) * 1e6
+    dc = torch.tensor(0.4, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tau = hybrid_rupture(dc, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J = 0.5 * ((tau - target) ** 2).sum()
+    (g,) = torch.autograd.grad(J, dc)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    # boundary-displacement gradient through the SBIM-only update (linear)
+    u = (torch.randn((steps, 3, n, n), device="cuda", generator=gen) * 1e-3).requires_grad_(True)
+    v = torch.zeros_like(u)
+    tgt = torch.randn((steps, 3, n, n), device="cuda", generator=gen) * 1e6
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    ts = sbim_sequence(u, v, n1=n, n3=n, L1=n * h, L3=n * h, cs=cs, cp=cp, rho=rho, dt=dt,
+                       n_cut=args.n_cut or 1024, side=1)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    (gu,) = torch.autograd.grad(0.5 * ((ts - tgt) ** 2).sum(), u)
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    line = {
+        "metric": "coupled Dc-gradient steps/s", "value": steps / (t2 - t0), "unit": "steps/s",
+        "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": 1e3 * (t2 - t0) / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"dJ/dDc through {steps} coupled steps, {n}x8x{n} slab, two SBIM "
+                               f"half-spaces, {kw['n_cut']}-lag history, checkpoints every 50; and "
+                               f"dJ/du through {steps} SBIM-only steps"},
+        "forward_ms_per_step": 1e3 * (t1 - t0) / steps,
+        "backward_ms_per_step": 1e3 * (t2 - t1) / steps,
+        "dJ_dDc": float(g),
+        "sbim_only": {"forward_ms_per_step": 1e3 * (t4 - t3) / steps,
+                      "backward_ms_per_step": 1e3 * (t5 - t4) / steps,
+                      "grad_norm": float(gu.norm())},
+        "note": "host wall clock around each pass (Python-driven loops, one sync per pass)",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -583,6 +650,8 @@ def main():
         run_coupled(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_native(args)
 

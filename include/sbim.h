@@ -328,6 +328,34 @@ int sbim_hybrid_step(sbim_hybrid h, const void* force);
  * last step (Pa). */
 int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* traction);
 
+/*
+ * Gradients through the coupled run (reverse sweep).  A forward run that keeps
+ * FE states every K steps (sbim_hybrid_get_state) and the boundary tractions of
+ * every step (sbim_hybrid_boundary_tractions) can recompute any step without the
+ * SBIM half-spaces (sbim_hybrid_step_given), and the transpose of each step is
+ * taken in reverse order by sbim_hybrid_adjoint_step.
+ *
+ * sbim_hybrid_boundary_tractions -- device copies [3][n3][n1] of the top and bottom
+ * SBIM tractions of the last step.
+ * sbim_hybrid_step_given -- one step with the given boundary tractions in place of
+ * the SBIM evaluation (the half-spaces are not advanced).
+ * sbim_hybrid_adjoint_step -- transpose of one step of the functional
+ * sum_n <tau_n, tau_bar_n> of the fault tractions tau_n (Eqs. (fepred)-(fecorr),
+ * (freeslip)-(stickslip), (slipweak), and the SBIM transposes).  h: a handle with
+ * the same parameters and fault law, used only for this sweep (its SBIM half-spaces
+ * take sbim_step_adjoint calls): call for steps N-1, ..., 0 in that order.
+ *   u, v, a           device, the state before step n  [L][3][n3][n1]
+ *   tau_top, tau_bot  device, that step's boundary tractions [3][n3][n1]
+ *   tau_bar           device, cotangent of the step's fault traction [3][n3][n1] (or NULL)
+ *   lu, lv, la        device, in: cotangent of the state after step n; out: before it
+ *   dc_bar            device [n3][n1], accumulates d/dDc (per fault node)
+ */
+int sbim_hybrid_boundary_tractions(sbim_hybrid h, void* tau_top, void* tau_bot);
+int sbim_hybrid_step_given(sbim_hybrid h, const void* tau_top, const void* tau_bot);
+int sbim_hybrid_adjoint_step(sbim_hybrid h, const void* u, const void* v, const void* a,
+                             const void* tau_top, const void* tau_bot, const void* tau_bar,
+                             void* lu, void* lv, void* la, void* dc_bar);
+
 /* sbim_hybrid_info -- node layers, steps taken, and the two SBIM handles (NULL
  * with free surfaces), e.g. for profiling or sbim_set_conv_config. */
 int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* top,

@@ -38,7 +38,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sbim_oracle import SBIMOracle
+from .sbim_oracle import SBIMAdjointOracle, SBIMOracle
 
 
 # ---------------------------------------------------------------------------
@@ -177,6 +177,7 @@ class HybridOracle:
             t_bot = self.bot.step(u_new[0], v_pred[0])["tau"]
             f[me.top] += A * t_top
             f[0] -= A * t_bot
+            self.last_tau_top, self.last_tau_bot = t_top, t_bot
         kint = self.fem.internal_force(u_new)
         if me.fault:                                                   # step 5
             p, q = me.f + 1, me.f
@@ -213,3 +214,114 @@ class HybridOracle:
         kin = 0.5 * np.sum(self.fem.mass * self.v ** 2)
         strain = 0.5 * np.sum(self.u * self.fem.internal_force(self.u))
         return kin, strain
+
+
+# ---------------------------------------------------------------------------
+# Gradient of a fault-traction misfit with respect to the slip-weakening
+# distance Dc through the coupled run (reverse sweep of Section 2.4's step).
+# ---------------------------------------------------------------------------
+def forward_record(o, steps):
+    """Run ``steps`` hybrid steps of the HybridOracle ``o`` and return the
+    states before each step and the fault tractions after each step."""
+    xs, taus = [], []
+    for _ in range(steps):
+        xs.append((o.u.copy(), o.v.copy(), o.a.copy()))
+        o.step()
+        taus.append(o.fault_traction.copy())
+    return xs, np.array(taus)
+
+
+def dc_gradient(mesh, cs, cp, rho, dt, n_cut, fault, xs, tau_bar):
+    """d/dDc of sum_n <tau_n, tau_bar_n> (tau_n: fault traction after step n),
+    per fault node, by the literal transpose of each step in reverse order.
+    xs: states (u, v, a) before each step (a forward run from these states with
+    the same parameters reproduces tau_n); tau_bar: [N][3][n3][n1].
+    Returns (dDc map [n3][n1], lambda_0 = (u_bar, v_bar, a_bar) of the initial
+    state)."""
+    fem = FEMOracle(mesh, cs, cp, rho)
+    m = fem.mass
+    A = mesh.h ** 2
+    L1, L3 = mesh.n1 * mesh.h, mesh.n3 * mesh.h
+    adj_top = SBIMAdjointOracle(mesh.n1, mesh.n3, L1, L3, cs, cp, rho, dt, n_cut, +1)
+    adj_bot = SBIMAdjointOracle(mesh.n1, mesh.n3, L1, L3, cs, cp, rho, dt, n_cut, -1)
+    # forward replay to recover the boundary tractions of every step
+    rep = HybridOracle(mesh, cs, cp, rho, dt, n_cut=n_cut, fault=fault)
+    rep.u, rep.v, rep.a = (x.copy() for x in xs[0])
+    t_top, t_bot = [], []
+    for _ in range(len(xs)):
+        rep.step()
+        t_top.append(rep.last_tau_top)
+        t_bot.append(rep.last_tau_bot)
+    p, q = mesh.f + 1, mesh.f
+    fl = fault
+    lu = np.zeros_like(xs[0][0]); lv = np.zeros_like(lu); la = np.zeros_like(lu)
+    dDc = np.zeros((mesh.n3, mesh.n1))
+    for n in range(len(xs) - 1, -1, -1):
+        u, v, a = xs[n]
+        # forward quantities of step n
+        v_pred = v + dt * a
+        u_new = u + dt * v + 0.5 * dt * dt * a
+        f = np.zeros_like(u)
+        f[mesh.top] += A * t_top[n]
+        f[0] -= A * t_bot[n]
+        a_free = (-fem.internal_force(u_new) + f) / m
+        vfree = v_pred - 0.5 * dt * a + dt * a_free
+        imp = dt * A * (1.0 / m[p] + 1.0 / m[q])
+        stick = (vfree[p] - vfree[q]) / imp
+        du = u_new[p] - u_new[q]
+        slip = np.hypot(du[0], du[2])
+        sig = fl.sigma0 - stick[1]
+        fric = fl.friction(slip)
+        S = sig * fric
+        t1, t3 = fl.tau0 + stick[0], stick[2]
+        mag = np.hypot(t1, t3)
+        over = mag > S
+        # corrector transpose: v' = v_pred + dt/2 (an - a), a' = an
+        l_vp = lv.copy()
+        l_an = 0.5 * dt * lv + la
+        l_a = -0.5 * dt * lv
+        l_un = lu.copy()
+        # fault forces: an[p] -= A tau / m[p], an[q] += A tau / m[q]
+        l_af = l_an.copy()
+        tb = -A / m[p] * l_an[p] + A / m[q] * l_an[q] + tau_bar[n]
+        # fault traction
+        l_stick = tb.copy()
+        magc = np.where(mag > 0, mag, 1.0)
+        th1, th3 = t1 / magc, t3 / magc
+        proj = th1 * tb[0] + th3 * tb[2]
+        l_t1 = S / magc * (tb[0] - th1 * proj)
+        l_t3 = S / magc * (tb[2] - th3 * proj)
+        l_S = proj
+        weak = slip < fl.Dc
+        dmu_dslip = np.where(weak, -(fl.mu_s - fl.mu_k) / fl.Dc, 0.0)
+        dmu_dDc = np.where(weak, (fl.mu_s - fl.mu_k) * slip / fl.Dc ** 2, 0.0)
+        l_stick[0] = np.where(over, l_t1, tb[0])
+        l_stick[2] = np.where(over, l_t3, tb[2])
+        l_stick[1] = tb[1] + np.where(over, -fric * l_S, 0.0)
+        l_slip = np.where(over, l_S * sig * dmu_dslip, 0.0)
+        dDc += np.where(over, l_S * sig * dmu_dDc, 0.0)
+        sl = np.where(slip > 0, slip, 1.0)
+        for c in (0, 2):
+            g = np.where(slip > 0, l_slip * du[c] / sl, 0.0)
+            l_un[p, c] += g
+            l_un[q, c] -= g
+        # stick = (vfree[p] - vfree[q]) / imp, vfree = v_pred - dt/2 a + dt a_free
+        for lay, sgn in ((p, 1.0), (q, -1.0)):
+            lvf = sgn * l_stick / imp
+            l_vp[lay] += lvf
+            l_a[lay] += -0.5 * dt * lvf
+            l_af[lay] += dt * lvf
+        # a_free = (-K u_new + f) / m
+        l_F = l_af / m
+        l_un += -fem.internal_force(l_F)
+        ub, vb = adj_top.step(A * l_F[mesh.top])
+        l_un[mesh.top] += ub
+        l_vp[mesh.top] += vb
+        ub, vb = adj_bot.step(-A * l_F[0])
+        l_un[0] += ub
+        l_vp[0] += vb
+        # predictor transpose: v_pred = v + dt a, u_new = u + dt v + dt^2/2 a
+        lu = l_un
+        lv = l_vp + dt * l_un
+        la = l_a + dt * l_vp + 0.5 * dt * dt * l_un
+    return dDc, (lu, lv, la)

@@ -557,3 +557,33 @@ def adjoint_sequence(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, tau_bar, kern
     coef = side * mat.mu / cs
     v_bar = -coef * mat.impedance[None, :, None, None] * tau_bar
     return u_bar, v_bar
+
+
+class SBIMAdjointOracle:
+    """Transpose of a sequence of updates taken one step at a time in reverse
+    time: ``step(tau_bar_m)`` for m = N-1, N-2, ... returns (u_bar_m, v_bar_m),
+    the same stage transposes as ``adjoint_sequence`` (which it equals)."""
+
+    def __init__(self, n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, kernel="table"):
+        self.n1, self.n3, self.n_cut, self.side = n1, n3, n_cut, side
+        self.mat = Material(cs, cp, rho)
+        modes = ModeSet.build(n1, n3, L1, L3)
+        dT = modes.q * cs * dt
+        kt = KernelTable(self.mat.eta, float(dT.max()) * max(n_cut - 1, 1) + 1.0)
+        uniq, inv = np.unique(dT, return_inverse=True)
+        wu = np.stack([trapezoid_weights(d, n_cut, kt) for d in uniq], axis=1)
+        A = modal_matrices(modes, self.mat, side, wu[:, inv, :])
+        self.AH = np.conj(np.swapaxes(A, 2, 3))
+        self.future = []          # G of the steps after the current one, nearest first
+
+    def step(self, tau_bar):
+        G = dft2_inverse_transpose(tau_bar).reshape(3, -1)
+        self.future.insert(0, G)
+        del self.future[self.n_cut:]
+        Ub = np.zeros_like(G)
+        for lag, Gl in enumerate(self.future):
+            Ub += np.einsum("qab,bq->aq", self.AH[lag], Gl)
+        nh = self.n1 // 2 + 1
+        u_bar = dft2_forward_transpose(Ub.reshape(3, self.n3, nh), self.n1)
+        v_bar = -(self.side * self.mat.mu / self.mat.cs) * self.mat.impedance[:, None, None] * tau_bar
+        return u_bar, v_bar

@@ -48,6 +48,82 @@ class SBIMSequence(torch.autograd.Function):
         return u_bar, v_bar, None
 
 
+class HybridRupture(torch.autograd.Function):
+    """Fault tractions [N, 3, n3, n1] of N coupled steps from rest (FE slab with a
+    slip-weakening fault between two SBIM half-spaces, Section 2.4) as a function
+    of the uniform slip-weakening distance Dc (a 0-d tensor).
+
+    Forward: keeps the FE state every K steps and the SBIM boundary tractions of
+    every step (the half-spaces' state is a linear function of the boundary
+    history, so these replace it).  Backward: for each K-step segment, latest
+    first, restores the checkpoint, recomputes the segment's states without the
+    half-spaces (sbim_hybrid_step_given), and takes the transpose of its steps in
+    reverse order (sbim_hybrid_adjoint_step), accumulating dJ/dDc per fault node
+    (summed for the uniform Dc).
+    """
+
+    @staticmethod
+    def forward(ctx, dc, params, law, steps, every):
+        from .hybrid import Hybrid
+        dcv = dc.detach().cpu().double().numpy()
+        if dcv.ndim:
+            raise ValueError("Dc must be a 0-d tensor (a uniform slip-weakening distance)")
+        h = Hybrid(**params)
+        try:
+            h.set_fault(law["mu_s"], law["tau0"], law["mu_k"], float(dcv), law["sigma0"])
+            ckpt, ttop, tbot, taus = {}, [], [], []
+            for n in range(steps):
+                if n % every == 0:
+                    ckpt[n] = h.get_state()
+                h.step()
+                top, bot = h.boundary_tractions()
+                ttop.append(top)
+                tbot.append(bot)
+                taus.append(h.fault_fields()[2])
+        finally:
+            h.close()
+        ctx.params, ctx.law, ctx.steps, ctx.every, ctx.dc = params, law, steps, every, float(dcv)
+        ctx.ckpt, ctx.ttop, ctx.tbot = ckpt, ttop, tbot
+        return torch.stack(taus)
+
+    @staticmethod
+    def backward(ctx, tau_bar):
+        from .hybrid import Hybrid
+        tau_bar = tau_bar.contiguous()
+        law = ctx.law
+        adj = Hybrid(**ctx.params)
+        rec = Hybrid(**ctx.params)
+        try:
+            for x in (adj, rec):
+                x.set_fault(law["mu_s"], law["tau0"], law["mu_k"], ctx.dc, law["sigma0"])
+            lu = torch.zeros(adj.shape, dtype=adj.dtype, device=tau_bar.device)
+            lv, la = torch.zeros_like(lu), torch.zeros_like(lu)
+            dcb = torch.zeros((adj.n3, adj.n1), dtype=adj.dtype, device=tau_bar.device)
+            for s0 in reversed(range(0, ctx.steps, ctx.every)):
+                s1 = min(s0 + ctx.every, ctx.steps)
+                rec.set_state(*ctx.ckpt[s0])
+                states = []
+                for n in range(s0, s1):
+                    states.append(rec.get_state())
+                    rec.step_given(ctx.ttop[n], ctx.tbot[n])
+                for n in range(s1 - 1, s0 - 1, -1):
+                    u, v, a = states[n - s0]
+                    adj.adjoint_step(u, v, a, ctx.ttop[n], ctx.tbot[n], tau_bar[n], lu, lv, la, dcb)
+        finally:
+            adj.close()
+            rec.close()
+        return dcb.sum().to(torch.float64), None, None, None, None
+
+
+def hybrid_rupture(dc, *, n1, n2, n3, h, cs, cp, rho, dt, n_cut, mu_s, tau0, mu_k, sigma0,
+                   steps, every=50, precision="fp32"):
+    """Differentiable fault tractions of a coupled rupture with respect to Dc."""
+    params = dict(n1=n1, n2=n2, n3=n3, h=h, cs=cs, cp=cp, rho=rho, dt=dt, n_cut=n_cut,
+                  precision=precision, boundaries=True, fault=True)
+    law = dict(mu_s=mu_s, tau0=tau0, mu_k=mu_k, sigma0=sigma0)
+    return HybridRupture.apply(dc, params, law, steps, every)
+
+
 def sbim_sequence(u, v, *, n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, precision="fp32",
                   kahan=True):
     """Differentiable tractions of N consecutive updates from rest."""

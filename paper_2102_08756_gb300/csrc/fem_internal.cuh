@@ -24,6 +24,28 @@ struct FaultArgs {
   R* traction;        // [3][n3][n1] output: fault traction perturbation (Pa), or NULL
 };
 
+// Buffers of the transpose of one step (all [L][3][n3][n1] unless noted).
+template <class R>
+struct AdjointArgs {
+  const R *u, *v, *a;         // state before the step
+  R *un, *vp, *af;            // recomputed u_new, v_pred, a_free
+  R *lu, *lv, *la;            // in: cotangent after the step; out: before
+  R *lun, *lvp, *lan, *lao;   // cotangents of u_new, v_pred, a_with_fault (then a_free), a
+  R* lF;                      // cotangent of the force
+  R *tb_top, *tb_bot;         // [3][n3][n1] cotangents of the SBIM tractions
+  const R* tau_bar;           // [3][n3][n1] cotangent of the fault traction output (or NULL)
+  R* ddc;                     // [n3][n1] accumulated d/dDc
+  R dt;
+  int weld;
+};
+
+// stage 0: recompute u_new, v_pred; 1: corrector transpose; 2: fault transpose;
+// 3: mass and SBIM cotangents; 4: stiffness transpose; 5: predictor transpose.
+template <class R>
+cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const FaultArgs<R>& fa,
+                           int stage, cudaStream_t st);
+template <class R> cudaError_t layer_add(R* dst, const R* src, long long n, cudaStream_t st);
+
 template <class R> cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st);
 template <class R>
 cudaError_t force(const R* u, R* an, const MeshArgs& g, const R* tau_top, const R* tau_bot,

@@ -168,6 +168,189 @@ __global__ void fault_fields_kernel(const R* __restrict__ u, const R* __restrict
   }
 }
 
+// ----------------------------------------------------------------------------
+// Transpose of one hybrid step (reverse sweep for gradients).  Notation: for a
+// forward quantity x, lx is the cotangent d(functional)/dx.
+// ----------------------------------------------------------------------------
+
+// u_new = u + dt v + dt^2/2 a, v_pred = v + dt a (into separate buffers)
+template <class R>
+__global__ void predict_to_kernel(const R* __restrict__ u, const R* __restrict__ v,
+                                  const R* __restrict__ a, R* __restrict__ un, R* __restrict__ vp,
+                                  long long n, R dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    un[i] = u[i] + dt * v[i] + (R)0.5 * dt * dt * a[i];
+    vp[i] = v[i] + dt * a[i];
+  }
+}
+
+// corrector transpose: lvp = lv, lan = dt/2 lv + la, la_out = -dt/2 lv; lun = lu
+template <class R>
+__global__ void adj_correct_kernel(const R* __restrict__ lu, const R* __restrict__ lv,
+                                   const R* __restrict__ la, R* __restrict__ lun,
+                                   R* __restrict__ lvp, R* __restrict__ lan, R* __restrict__ lao,
+                                   long long n, R dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R x = lv[i];
+    lun[i] = lu[i];
+    lvp[i] = x;
+    lan[i] = (R)0.5 * dt * x + la[i];
+    lao[i] = -(R)0.5 * dt * x;
+  }
+}
+
+// Fault transpose at one split node.  Recomputes the forward fault quantities
+// from u_new, v_pred, a, a_free; lan enters as the cotangent of the
+// accelerations with fault forces and leaves (on the two fault layers) as that
+// of a_free; adds to lun (slip), lvp and lao (free slip-rate predictor), and
+// dDc (strength).
+template <class R>
+__global__ void adj_fault_kernel(const R* __restrict__ un, const R* __restrict__ vp,
+                                 const R* __restrict__ a, const R* __restrict__ af,
+                                 R* __restrict__ lan, R* __restrict__ lun, R* __restrict__ lvp,
+                                 R* __restrict__ lao, const R* __restrict__ tau_bar,
+                                 R* __restrict__ ddc, MeshArgs g, FaultArgs<R> fa, R dt, int weld) {
+  const long long plane = (long long)g.n1 * g.n3;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const long long P = (long long)(g.f + 1) * 3 * plane + q;
+  const long long M = (long long)g.f * 3 * plane + q;
+  const R m = (R)g.half_mass;
+  const R A = (R)g.area;
+  const R imp = dt * A * ((R)2 / m);
+  R stick[3], du[3], tb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long o = c * plane;
+    const R vfp = vp[P + o] - (R)0.5 * dt * a[P + o] + dt * af[P + o];
+    const R vfm = vp[M + o] - (R)0.5 * dt * a[M + o] + dt * af[M + o];
+    stick[c] = (vfp - vfm) / imp;
+    du[c] = un[P + o] - un[M + o];
+    tb[c] = -A / m * lan[P + o] + A / m * lan[M + o] + (tau_bar ? tau_bar[o + q] : (R)0);
+  }
+  R ls[3] = {tb[0], tb[1], tb[2]};
+  if (!weld) {
+    const R slip = sqrt(du[0] * du[0] + du[2] * du[2]);
+    const R mus = fa.mu_s[q];
+    const bool weak = slip < fa.Dc;
+    const R fric = weak ? mus - (mus - fa.mu_k) * slip / fa.Dc : fa.mu_k;
+    const R sig = fa.sigma0 - stick[1];
+    const R S = sig * fric;
+    const R t1 = fa.tau0[q] + stick[0], t3 = stick[2];
+    const R mag = sqrt(t1 * t1 + t3 * t3);
+    if (mag > S) {
+      const R th1 = t1 / mag, th3 = t3 / mag;
+      const R proj = th1 * tb[0] + th3 * tb[2];
+      ls[0] = S / mag * (tb[0] - th1 * proj);
+      ls[2] = S / mag * (tb[2] - th3 * proj);
+      ls[1] = tb[1] - fric * proj;
+      const R dmu_dslip = weak ? -(mus - fa.mu_k) / fa.Dc : (R)0;
+      const R dmu_ddc = weak ? (mus - fa.mu_k) * slip / (fa.Dc * fa.Dc) : (R)0;
+      ddc[q] += proj * sig * dmu_ddc;
+      const R lslip = proj * sig * dmu_dslip;
+      if (slip > (R)0) {
+        lun[P] += lslip * du[0] / slip;
+        lun[M] -= lslip * du[0] / slip;
+        lun[P + 2 * plane] += lslip * du[2] / slip;
+        lun[M + 2 * plane] -= lslip * du[2] / slip;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long o = c * plane;
+    const R lvf = ls[c] / imp;
+    lvp[P + o] += lvf;
+    lvp[M + o] -= lvf;
+    lao[P + o] -= (R)0.5 * dt * lvf;
+    lao[M + o] += (R)0.5 * dt * lvf;
+    lan[P + o] += dt * lvf;    // from here on: the cotangent of a_free
+    lan[M + o] -= dt * lvf;
+  }
+}
+
+// lF = laf / m (per layer), and the SBIM cotangents tb_top = A lF[top],
+// tb_bot = -A lF[0]
+template <class R>
+__global__ void adj_mass_kernel(const R* __restrict__ laf, R* __restrict__ lF, MeshArgs g,
+                                R* __restrict__ tb_top, R* __restrict__ tb_bot) {
+  const long long plane = (long long)g.n1 * g.n3;
+  const long long n = (long long)g.L * 3 * plane;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(i / (3 * plane));
+    const bool down = l > 0 && !(g.fault && l == g.f + 1);
+    const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+    const R m = (down ? (R)g.half_mass : (R)0) + (up ? (R)g.half_mass : (R)0);
+    const R x = laf[i] / m;
+    lF[i] = x;
+    const long long r = i - (long long)l * 3 * plane;
+    if (tb_top && l == g.L - 1) tb_top[r] = (R)g.area * x;
+    if (tb_bot && l == 0) tb_bot[r] = -(R)g.area * x;
+  }
+}
+
+// out += -K x (the stiffness is symmetric: this is the transpose of -K u)
+template <class R>
+__global__ void stiffness_add_kernel(const R* __restrict__ x, R* __restrict__ out, MeshArgs g) {
+  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i3 = blockIdx.y;
+  const int l = blockIdx.z;
+  if (i1 >= g.n1) return;
+  const long long plane = (long long)g.n1 * g.n3;
+  const R* __restrict__ S = reinterpret_cast<const R*>(g.stencil);
+  const bool down = l > 0 && !(g.fault && l == g.f + 1);
+  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+  R F[3] = {(R)0, (R)0, (R)0};
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? !down : !up) continue;
+    const int base = side * 18 * 9;
+    for (int oy = 0; oy < 2; ++oy) {
+      const int ly = l + (side == 0 ? oy - 1 : oy);
+      const R* xl = x + (long long)ly * 3 * plane;
+      for (int oz = 0; oz < 3; ++oz) {
+        int j3 = i3 + oz - 1;
+        j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
+        for (int ox = 0; ox < 3; ++ox) {
+          int j1 = i1 + ox - 1;
+          j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
+          const long long qq = (long long)j3 * g.n1 + j1;
+          const R x0 = xl[qq], x1 = xl[plane + qq], x2 = xl[2 * plane + qq];
+          const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
+          for (int c = 0; c < 3; ++c)
+            F[c] -= S[s + 3 * c] * x0 + S[s + 3 * c + 1] * x1 + S[s + 3 * c + 2] * x2;
+        }
+      }
+    }
+  }
+  R* ol = out + (long long)l * 3 * plane + (long long)i3 * g.n1 + i1;
+  for (int c = 0; c < 3; ++c) ol[c * plane] += F[c];
+}
+
+// dst[layer][...] += src[...] on one layer (boundary cotangents from the SBIM transposes)
+template <class R>
+__global__ void layer_add_kernel(R* __restrict__ dst, const R* __restrict__ src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
+// predictor transpose: lu = lun, lv = lvp + dt lun, la = lao + dt lvp + dt^2/2 lun
+template <class R>
+__global__ void adj_predict_kernel(const R* __restrict__ lun, const R* __restrict__ lvp,
+                                   const R* __restrict__ lao, R* __restrict__ lu,
+                                   R* __restrict__ lv, R* __restrict__ la, long long n, R dt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R x = lun[i], y = lvp[i];
+    lu[i] = x;
+    lv[i] = y + dt * x;
+    la[i] = lao[i] + dt * y + (R)0.5 * dt * dt * x;
+  }
+}
+
 unsigned grid1(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)(b > 152 * 32 ? 152 * 32 : b);
@@ -212,6 +395,51 @@ cudaError_t fault_fields(const R* u, const R* v, const MeshArgs& g, R* slip, R* 
   return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const FaultArgs<R>& fa,
+                           int stage, cudaStream_t st) {
+  const long long n = (long long)g.L * 3 * g.n1 * g.n3;
+  const long long plane = (long long)g.n1 * g.n3;
+  const R dt = j.dt;
+  switch (stage) {
+    case 0:
+      predict_to_kernel<R><<<grid1(n, 256), 256, 0, st>>>(j.u, j.v, j.a, j.un, j.vp, n, dt);
+      break;
+    case 1:
+      adj_correct_kernel<R><<<grid1(n, 256), 256, 0, st>>>(j.lu, j.lv, j.la, j.lun, j.lvp, j.lan,
+                                                             j.lao, n, dt);
+      break;
+    case 2:
+      if (g.fault)
+        adj_fault_kernel<R><<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(
+            j.un, j.vp, j.a, j.af, j.lan, j.lun, j.lvp, j.lao, j.tau_bar, j.ddc, g, fa, dt,
+            j.weld);
+      break;
+    case 3:
+      adj_mass_kernel<R><<<grid1(n, 256), 256, 0, st>>>(j.lan, j.lF, g, j.tb_top, j.tb_bot);
+      break;
+    case 4: {
+      const int tx = g.n1 >= 128 ? 128 : 32;
+      const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
+      stiffness_add_kernel<R><<<grid, tx, 0, st>>>(j.lF, j.lun, g);
+      break;
+    }
+    case 5:
+      adj_predict_kernel<R><<<grid1(n, 256), 256, 0, st>>>(j.lun, j.lvp, j.lao, j.lu, j.lv, j.la,
+                                                             n, dt);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t layer_add(R* dst, const R* src, long long n, cudaStream_t st) {
+  layer_add_kernel<R><<<grid1(n, 256), 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 #define SBIM_FEM_INST(R)                                                                     \
   template cudaError_t predict<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
   template cudaError_t force<R>(const R*, R*, const MeshArgs&, const R*, const R*, const R*, \
@@ -219,7 +447,10 @@ cudaError_t fault_fields(const R* u, const R* v, const MeshArgs& g, R* slip, R* 
   template cudaError_t fault<R>(const R*, const R*, const R*, R*, const MeshArgs&,           \
                                 const FaultArgs<R>&, R, int, cudaStream_t);                  \
   template cudaError_t correct<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
-  template cudaError_t fault_fields<R>(const R*, const R*, const MeshArgs&, R*, R*, cudaStream_t);
+  template cudaError_t fault_fields<R>(const R*, const R*, const MeshArgs&, R*, R*, cudaStream_t); \
+  template cudaError_t adjoint_stages<R>(const AdjointArgs<R>&, const MeshArgs&,                  \
+                                         const FaultArgs<R>&, int, cudaStream_t);                \
+  template cudaError_t layer_add<R>(R*, const R*, long long, cudaStream_t);
 SBIM_FEM_INST(float)
 SBIM_FEM_INST(double)
 

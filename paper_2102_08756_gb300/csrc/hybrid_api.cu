@@ -33,6 +33,8 @@ struct sbim_hybrid_ctx {
   void* tau0 = nullptr;
   void* traction = nullptr;
   void* stencil = nullptr;
+  void* adj[8] = {};        // reverse sweep: un, vp, af, lun, lvp, lan, lao, lF
+  void* adjp[4] = {};       // tb_top, tb_bot, ub, vb ([3][n3][n1])
   double mu_k = 0, Dc = 1, sigma0 = 0;
   bool have_law = false;
   long long n = 0;
@@ -201,6 +203,68 @@ int step_impl(sbim_hybrid_ctx* c, const void* src) {
   return rc;
 }
 
+template <class R>
+int step_given_impl(sbim_hybrid_ctx* c, const void* tau_top, const void* tau_bot) {
+  int rc = stage_predict<R>(c);
+  if (rc != SBIM_OK) return rc;
+  if (tau_top && tau_bot) {
+    const size_t pb = 3 * c->plane() * c->rs;
+    HCU(cudaMemcpyAsync(c->tau_top, tau_top, pb, cudaMemcpyDeviceToDevice, c->stream));
+    HCU(cudaMemcpyAsync(c->tau_bot, tau_bot, pb, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  rc = stage_finish<R>(c, nullptr);
+  if (rc == SBIM_OK) ++c->n;
+  return rc;
+}
+
+template <class R>
+int adjoint_impl(sbim_hybrid_ctx* c, const void* u, const void* v, const void* a,
+                 const void* tau_top, const void* tau_bot, const void* tau_bar, void* lu, void* lv,
+                 void* la, void* dc_bar) {
+  cudaStream_t st = c->stream;
+  const size_t fb = c->elems() * c->rs, pb = 3 * c->plane() * c->rs;
+  for (void*& x : c->adj)
+    if (!x) HCU(cudaMalloc(&x, fb));
+  for (void*& x : c->adjp)
+    if (!x) HCU(cudaMalloc(&x, pb));
+  sbim::fem::AdjointArgs<R> j;
+  j.u = (const R*)u; j.v = (const R*)v; j.a = (const R*)a;
+  j.un = (R*)c->adj[0]; j.vp = (R*)c->adj[1]; j.af = (R*)c->adj[2];
+  j.lu = (R*)lu; j.lv = (R*)lv; j.la = (R*)la;
+  j.lun = (R*)c->adj[3]; j.lvp = (R*)c->adj[4]; j.lan = (R*)c->adj[5]; j.lao = (R*)c->adj[6];
+  j.lF = (R*)c->adj[7];
+  j.tb_top = c->boundaries ? (R*)c->adjp[0] : nullptr;
+  j.tb_bot = c->boundaries ? (R*)c->adjp[1] : nullptr;
+  j.tau_bar = (const R*)tau_bar;
+  j.ddc = (R*)dc_bar;
+  j.dt = (R)c->dt;
+  j.weld = c->have_law ? 0 : 1;
+  const sbim::fem::MeshArgs g = mesh_args(c);
+  sbim::fem::FaultArgs<R> fa;
+  fa.mu_s = (const R*)c->mu_s; fa.tau0 = (const R*)c->tau0;
+  fa.mu_k = (R)c->mu_k; fa.Dc = (R)c->Dc; fa.sigma0 = (R)c->sigma0; fa.traction = nullptr;
+  HCU(sbim::fem::adjoint_stages<R>(j, g, fa, 0, st));
+  HCU(sbim::fem::force<R>(j.un, j.af, g, c->boundaries ? (const R*)tau_top : nullptr,
+                          c->boundaries ? (const R*)tau_bot : nullptr, nullptr, st));
+  for (int stage = 1; stage <= 4; ++stage) HCU(sbim::fem::adjoint_stages<R>(j, g, fa, stage, st));
+  if (c->boundaries) {
+    const long long lay = 3 * c->plane();
+    R* ub = (R*)c->adjp[2];
+    R* vb = (R*)c->adjp[3];
+    int rc = sbim_step_adjoint(c->top, j.tb_top, ub, vb);
+    if (rc != SBIM_OK) return rc;
+    HCU(sbim::fem::layer_add<R>(j.lun + (c->L - 1) * lay, ub, lay, st));
+    HCU(sbim::fem::layer_add<R>(j.lvp + (c->L - 1) * lay, vb, lay, st));
+    rc = sbim_step_adjoint(c->bot, j.tb_bot, ub, vb);
+    if (rc != SBIM_OK) return rc;
+    HCU(sbim::fem::layer_add<R>(j.lun, ub, lay, st));
+    HCU(sbim::fem::layer_add<R>(j.lvp, vb, lay, st));
+  }
+  HCU(sbim::fem::adjoint_stages<R>(j, g, fa, 5, st));
+  ++c->n;
+  return SBIM_OK;
+}
+
 void hrelease(sbim_hybrid_ctx* c) {
   if (!c) return;
   sbim_destroy(c->top);
@@ -208,6 +272,10 @@ void hrelease(sbim_hybrid_ctx* c) {
   void* p[] = {c->u,     c->v,     c->a,        c->an,      c->tau_top,
                c->tau_bot, c->mu_s, c->tau0, c->traction, c->stencil};
   for (void* x : p)
+    if (x) cudaFree(x);
+  for (void* x : c->adj)
+    if (x) cudaFree(x);
+  for (void* x : c->adjp)
     if (x) cudaFree(x);
   delete c;
 }
@@ -320,6 +388,36 @@ int sbim_hybrid_get_state(sbim_hybrid h, void* u, void* v, void* a) {
 int sbim_hybrid_step(sbim_hybrid h, const void* force) {
   if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
   return h->prec == SBIM_FP64 ? step_impl<double>(h, force) : step_impl<float>(h, force);
+}
+
+int sbim_hybrid_step_given(sbim_hybrid h, const void* tau_top, const void* tau_bot) {
+  if (!h) return hfail(SBIM_ERR_ARG, "NULL handle");
+  if (h->boundaries && (!tau_top || !tau_bot))
+    return hfail(SBIM_ERR_ARG, "a handle with SBIM boundaries needs both boundary tractions");
+  return h->prec == SBIM_FP64 ? step_given_impl<double>(h, tau_top, tau_bot)
+                              : step_given_impl<float>(h, tau_top, tau_bot);
+}
+
+int sbim_hybrid_boundary_tractions(sbim_hybrid h, void* tau_top, void* tau_bot) {
+  if (!h || !tau_top || !tau_bot) return hfail(SBIM_ERR_ARG, "NULL argument");
+  if (!h->boundaries) return hfail(SBIM_ERR_STATE, "the handle has free surfaces");
+  const size_t pb = 3 * h->plane() * h->rs;
+  HCU(cudaMemcpyAsync(tau_top, h->tau_top, pb, cudaMemcpyDeviceToDevice, h->stream));
+  HCU(cudaMemcpyAsync(tau_bot, h->tau_bot, pb, cudaMemcpyDeviceToDevice, h->stream));
+  return SBIM_OK;
+}
+
+int sbim_hybrid_adjoint_step(sbim_hybrid h, const void* u, const void* v, const void* a,
+                             const void* tau_top, const void* tau_bot, const void* tau_bar,
+                             void* lu, void* lv, void* la, void* dc_bar) {
+  if (!h || !u || !v || !a || !lu || !lv || !la || !dc_bar)
+    return hfail(SBIM_ERR_ARG, "NULL argument");
+  if (h->boundaries && (!tau_top || !tau_bot))
+    return hfail(SBIM_ERR_ARG, "a handle with SBIM boundaries needs both boundary tractions");
+  if (!h->fault) return hfail(SBIM_ERR_STATE, "the handle was created without a fault");
+  return h->prec == SBIM_FP64
+             ? adjoint_impl<double>(h, u, v, a, tau_top, tau_bot, tau_bar, lu, lv, la, dc_bar)
+             : adjoint_impl<float>(h, u, v, a, tau_top, tau_bot, tau_bar, lu, lv, la, dc_bar);
 }
 
 int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* traction) {

@@ -56,6 +56,26 @@ class Hybrid:
     def step(self, force=None):
         B.sbim_hybrid_step(self.h, None if force is None else self._t(force, self.shape))
 
+    def boundary_tractions(self):
+        t = self.torch
+        top = t.empty((3, self.n3, self.n1), dtype=self.dtype, device=self.stream.device)
+        bot = t.empty_like(top)
+        B.sbim_hybrid_boundary_tractions(self.h, top.data_ptr(), bot.data_ptr())
+        return top, bot
+
+    def step_given(self, tau_top, tau_bot):
+        shp = (3, self.n3, self.n1)
+        B.sbim_hybrid_step_given(self.h, self._t(tau_top, shp), self._t(tau_bot, shp))
+
+    def adjoint_step(self, u, v, a, tau_top, tau_bot, tau_bar, lu, lv, la, dc_bar):
+        shp = (3, self.n3, self.n1)
+        B.sbim_hybrid_adjoint_step(
+            self.h, self._t(u, self.shape), self._t(v, self.shape), self._t(a, self.shape),
+            self._t(tau_top, shp), self._t(tau_bot, shp),
+            None if tau_bar is None else self._t(tau_bar, shp),
+            self._t(lu, self.shape), self._t(lv, self.shape), self._t(la, self.shape),
+            self._t(dc_bar, (self.n3, self.n1)))
+
     def fault_fields(self):
         t = self.torch
         out = [t.empty((3, self.n3, self.n1), dtype=self.dtype, device=self.stream.device)

@@ -61,6 +61,9 @@ def lib():
     L.sbim_hybrid_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ll),
                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.sbim_hybrid_destroy.argtypes = [vp]
+    L.sbim_hybrid_boundary_tractions.argtypes = [vp, vp, vp]
+    L.sbim_hybrid_step_given.argtypes = [vp, vp, vp]
+    L.sbim_hybrid_adjoint_step.argtypes = [vp] * 11
     L.sbim_batch_create.argtypes = [ctypes.POINTER(vp), i] + [vp] * 10 + [i, i, vp]
     L.sbim_batch_step.argtypes = [vp, vp, vp, vp]
     L.sbim_batch_capture.argtypes = [vp, vp, vp, vp]
@@ -80,7 +83,8 @@ def lib():
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
                  "sbim_hybrid_step", "sbim_hybrid_fault_fields", "sbim_hybrid_info",
-                 "sbim_hybrid_destroy", "sbim_batch_create", "sbim_batch_step",
+                 "sbim_hybrid_destroy", "sbim_hybrid_boundary_tractions", "sbim_hybrid_step_given",
+                 "sbim_hybrid_adjoint_step", "sbim_batch_create", "sbim_batch_step",
                  "sbim_batch_capture", "sbim_batch_replay", "sbim_batch_member",
                  "sbim_batch_destroy", "sbim_hybrid_batch_create", "sbim_hybrid_batch_step",
                  "sbim_hybrid_batch_capture", "sbim_hybrid_batch_replay",
@@ -272,6 +276,19 @@ def sbim_hybrid_info(h):
     _check(lib().sbim_hybrid_info(h, ctypes.byref(layers), ctypes.byref(steps),
                                   ctypes.byref(top), ctypes.byref(bot)))
     return layers.value, steps.value, top, bot
+
+
+def sbim_hybrid_boundary_tractions(h, top_ptr, bot_ptr):
+    _check(lib().sbim_hybrid_boundary_tractions(h, top_ptr, bot_ptr))
+
+
+def sbim_hybrid_step_given(h, top_ptr, bot_ptr):
+    _check(lib().sbim_hybrid_step_given(h, top_ptr, bot_ptr))
+
+
+def sbim_hybrid_adjoint_step(h, u, v, a, tau_top, tau_bot, tau_bar, lu, lv, la, dc_bar):
+    _check(lib().sbim_hybrid_adjoint_step(h, u, v, a, tau_top, tau_bot, tau_bar, lu, lv, la,
+                                          dc_bar))
 
 
 def sbim_hybrid_destroy(h):
