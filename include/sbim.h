@@ -137,6 +137,30 @@ int sbim_reset(sbim_handle h);
 int sbim_get_step(sbim_handle h, long long* n);
 
 /*
+ * sbim_save / sbim_load -- checkpoint and restore the handle's state: the step
+ * counter n, the far-field traction and the whole history ring (the spectra of
+ * every displacement the truncated convolution of Eq. (SBI) can still reach;
+ * Section 2.3).  A run restored from a checkpoint continues bit-for-bit as the
+ * original run did from the step it was taken at.
+ *
+ *   sbim_save(h, buf, &bytes)
+ *     buf == NULL: writes the size a checkpoint needs to *bytes and returns OK.
+ *     Otherwise buf is host memory of capacity *bytes; if it is too small the
+ *     call writes the needed size to *bytes and fails with SBIM_ERR_ARG.  On
+ *     success *bytes is the size written.  Synchronises the handle's stream.
+ *   sbim_load(h, buf, bytes)
+ *     buf holds a checkpoint written by sbim_save of a handle with the same
+ *     n1, n3, L1, L3, c_s, c_p, rho, dt, n_cut, side and precision; anything else
+ *     (wrong magic, version, parameters or size) fails with SBIM_ERR_ARG and leaves
+ *     the handle unchanged.  Synchronises the handle's stream; buf may be freed on
+ *     return.  The caller owns buf in both calls.
+ * A checkpoint holds the raw history layout of this library build and is not a
+ * portable file format.
+ */
+int sbim_save(sbim_handle h, void* buf, size_t* bytes);
+int sbim_load(sbim_handle h, const void* buf, size_t bytes);
+
+/*
  * sbim_get_info -- sizes of the handle's spectral work, for throughput
  * accounting.  Any pointer may be NULL.
  *   n_modes     half-spectrum Fourier bins, n3 (n1/2 + 1)

@@ -710,6 +710,78 @@ int sbim_get_step(sbim_handle h, long long* n) {
   return SBIM_OK;
 }
 
+namespace {
+// Checkpoint header: the parameters a restored handle must match, then the state.
+struct SaveHeader {
+  char magic[8];
+  int version, n1, n3, n_cut, side, prec, n_orb_pad, pad0;
+  double L1, L3, cs, cp, rho, dt;
+  long long n, hist_bytes;
+  double tau_inf[3];
+};
+constexpr char kSaveMagic[8] = {'S', 'B', 'I', 'M', 'H', 'S', 'T', '1'};
+constexpr int kSaveVersion = 1;
+
+SaveHeader make_header(const sbim_ctx& c) {
+  SaveHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kSaveMagic, 8);
+  hd.version = kSaveVersion;
+  hd.n1 = c.n1; hd.n3 = c.n3; hd.n_cut = c.n_cut; hd.side = c.side; hd.prec = c.prec;
+  hd.n_orb_pad = c.n_orb_pad;
+  hd.L1 = c.L1; hd.L3 = c.L3; hd.cs = c.cs; hd.cp = c.cp; hd.rho = c.rho; hd.dt = c.dt;
+  hd.n = c.n;
+  hd.hist_bytes = (long long)c.hist_bytes;
+  for (int i = 0; i < 3; ++i) hd.tau_inf[i] = c.tau_inf[i];
+  return hd;
+}
+}  // namespace
+
+int sbim_save(sbim_handle h, void* buf, size_t* bytes) {
+  if (!h || !bytes) return fail(SBIM_ERR_ARG, "NULL argument");
+  const size_t need = sizeof(SaveHeader) + h->hist_bytes;
+  if (!buf) {
+    *bytes = need;
+    return SBIM_OK;
+  }
+  if (*bytes < need) {
+    const size_t have = *bytes;
+    *bytes = need;
+    return fail(SBIM_ERR_ARG, "checkpoint buffer holds %zu bytes, %zu needed", have, need);
+  }
+  const SaveHeader hd = make_header(*h);
+  std::memcpy(buf, &hd, sizeof(hd));
+  CU(cudaMemcpyAsync((char*)buf + sizeof(hd), h->d_hist, h->hist_bytes, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  *bytes = need;
+  return SBIM_OK;
+}
+
+int sbim_load(sbim_handle h, const void* buf, size_t bytes) {
+  if (!h || !buf) return fail(SBIM_ERR_ARG, "NULL argument");
+  if (bytes < sizeof(SaveHeader)) return fail(SBIM_ERR_ARG, "checkpoint is truncated");
+  SaveHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  const SaveHeader me = make_header(*h);
+  if (std::memcmp(hd.magic, kSaveMagic, 8) != 0) return fail(SBIM_ERR_ARG, "not a checkpoint");
+  if (hd.version != kSaveVersion) return fail(SBIM_ERR_ARG, "checkpoint version %d", hd.version);
+  if (hd.n1 != me.n1 || hd.n3 != me.n3 || hd.n_cut != me.n_cut || hd.side != me.side ||
+      hd.prec != me.prec || hd.n_orb_pad != me.n_orb_pad || hd.L1 != me.L1 || hd.L3 != me.L3 ||
+      hd.cs != me.cs || hd.cp != me.cp || hd.rho != me.rho || hd.dt != me.dt ||
+      hd.hist_bytes != me.hist_bytes)
+    return fail(SBIM_ERR_ARG, "checkpoint was taken from a handle with other parameters");
+  if (hd.n < 0) return fail(SBIM_ERR_ARG, "checkpoint step counter is negative");
+  if (bytes < sizeof(hd) + (size_t)hd.hist_bytes) return fail(SBIM_ERR_ARG, "checkpoint is truncated");
+  CU(cudaMemcpyAsync(h->d_hist, (const char*)buf + sizeof(hd), h->hist_bytes,
+                     cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->d_step, &hd.n, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->n = hd.n;
+  for (int i = 0; i < 3; ++i) h->tau_inf[i] = hd.tau_inf[i];
+  return SBIM_OK;
+}
+
 int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots, long long* hist_bytes,
                   long long* table_nodes) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");

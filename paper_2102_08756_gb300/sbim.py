@@ -45,6 +45,8 @@ def lib():
     L.sbim_reset.argtypes = [vp]
     L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
+    L.sbim_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.sbim_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.sbim_set_profiling.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
     L.sbim_set_conv_config.argtypes = [vp, i, i]
@@ -138,6 +140,24 @@ def sbim_get_info(h):
     vals = [ctypes.c_longlong() for _ in range(4)]
     _check(lib().sbim_get_info(h, *[ctypes.byref(v) for v in vals]))
     return dict(zip(("n_modes", "n_slots", "hist_bytes", "table_nodes"), (v.value for v in vals)))
+
+
+def sbim_save(h):
+    """Checkpoint of the handle's state as a numpy uint8 array."""
+    import numpy as np
+    n = ctypes.c_size_t(0)
+    _check(lib().sbim_save(h, None, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(lib().sbim_save(h, buf.ctypes.data, ctypes.byref(n)))
+    return buf[:n.value]
+
+
+def sbim_load(h, buf):
+    import numpy as np
+    if isinstance(buf, (bytes, bytearray, memoryview)):
+        buf = np.frombuffer(buf, dtype=np.uint8)
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().sbim_load(h, buf.ctypes.data if buf.nbytes else None, buf.nbytes))
 
 
 def sbim_set_profiling(h, enable):
@@ -359,6 +379,13 @@ class SBIM:
 
     def set_far_field(self, tau_inf):
         sbim_set_far_field(self.h, tau_inf)
+
+    def save(self):
+        """Checkpoint (numpy uint8) of the step counter, far field and history."""
+        return sbim_save(self.h)
+
+    def load(self, buf):
+        sbim_load(self.h, buf)
 
     def reset(self):
         sbim_reset(self.h)

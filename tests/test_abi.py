@@ -68,4 +68,8 @@ def test_null_handle_calls_fail_cleanly(lib):
         sbim.sbim_step(None, None, None, None)
     with pytest.raises(sbim.SBIMError):
         sbim.sbim_get_step(None)
+    with pytest.raises(sbim.SBIMError):
+        sbim.sbim_save(None)
+    with pytest.raises(sbim.SBIMError):
+        sbim.sbim_load(None, b"")
     sbim.sbim_destroy(None)

@@ -1,0 +1,83 @@
+"""Checkpoint and restore of an SBIM handle (sbim_save / sbim_load): the state of
+the truncated convolution of Eq. (SBI) is the step counter and the history ring;
+a run restored from a checkpoint must continue bit-for-bit."""
+import numpy as np
+import pytest
+
+from paper_2102_08756_gb300.synth import separable_history
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CS, CP, RHO = 3464.0, 6000.0, 2670.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _make(n1, n3, n_cut, precision, side=1, dt=None):
+    from paper_2102_08756_gb300.sbim import SBIM
+    L = 100.0 * n1
+    dt = dt or 0.3 * 100.0 / CP
+    return SBIM(n1, n3, L, 100.0 * n3, CS, CP, RHO, dt, n_cut, side, precision, 1)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16x2", "bf16"])
+@pytest.mark.parametrize("n_cut,split", [(7, 11), (24, 9)])
+def test_restore_continues_bit_exact(precision, n_cut, split):
+    n1, n3, steps = 24, 16, 20
+    dt = 0.3 * 100.0 / CP
+    hist = separable_history(n1, n3, 100.0 * n1, 100.0 * n3, steps, dt, CS, seed=7)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    a = _make(n1, n3, n_cut, precision)
+    a.set_far_field((1.5e6, -2.0e6, 3.0e5))
+    fields = [(torch.from_numpy(hist.u(m)).to("cuda", tdt), torch.from_numpy(hist.v(m)).to("cuda", tdt))
+              for m in range(steps)]
+    for m in range(split):
+        a.step(*fields[m])
+    ck = a.save()
+    first = [a.step(*fields[m]).cpu().numpy() for m in range(split, steps)]
+
+    b = _make(n1, n3, n_cut, precision)          # fresh handle, far field from the checkpoint
+    b.load(ck)
+    assert b.n == split
+    second = [b.step(*fields[m]).cpu().numpy() for m in range(split, steps)]
+    a.load(ck)                                   # the same handle, rewound
+    third = [a.step(*fields[m]).cpu().numpy() for m in range(split, steps)]
+    for x, y, z in zip(first, second, third):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+def test_load_rejects_other_parameters_and_garbage():
+    from paper_2102_08756_gb300.sbim import SBIMError
+    a = _make(16, 16, 8, "fp32")
+    z = torch.zeros((3, 16, 16), device="cuda")
+    a.step(z, z)
+    ck = a.save()
+    for other in (_make(16, 16, 9, "fp32"), _make(16, 16, 8, "fp64"), _make(16, 16, 8, "fp32", side=-1),
+                  _make(16, 16, 8, "fp32", dt=0.004), _make(16, 8, 8, "fp32")):
+        with pytest.raises(SBIMError) as e:
+            other.load(ck)
+        assert e.value.code == -1
+        assert other.n == 0
+    bad = ck.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(SBIMError):
+        a.load(bad)
+    with pytest.raises(SBIMError):
+        a.load(ck[:-1])
+    assert a.n == 1
+    from paper_2102_08756_gb300 import sbim
+    import ctypes
+    need = ctypes.c_size_t(0)
+    sbim._check(sbim.lib().sbim_save(a.h, None, ctypes.byref(need)))
+    small = np.empty(need.value - 1, dtype=np.uint8)
+    cap = ctypes.c_size_t(small.nbytes)
+    with pytest.raises(SBIMError):
+        sbim._check(sbim.lib().sbim_save(a.h, small.ctypes.data, ctypes.byref(cap)))
+    assert cap.value == need.value
