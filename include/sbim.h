@@ -298,6 +298,60 @@ int sbim_batch_member(sbim_batch b, int i, sbim_handle* h);
 int sbim_batch_destroy(sbim_batch b);
 
 /* ------------------------------------------------------------------------- */
+/* Pure-SBIM planar fault (Sections 2.1, 2.3 and 3): the boundary-only       */
+/* solver the hybrid scheme is verified against on TPV3.                     */
+/* ------------------------------------------------------------------------- */
+typedef struct sbim_fault_ctx* sbim_fault;
+
+/*
+ * sbim_fault_create -- a planar fault x2 = 0 between two identical elastic
+ * half-spaces, each represented only by its boundary through Eq. (SBI) (an
+ * upper, side +1, and a lower, side -1, sbim_handle of the given parameters; the
+ * paper describes no steps for this solver, which are):
+ *   (1) u+-_{n+1} = u+-_n + dt v+-_n on the two faces;
+ *   (2) S+- = the non-local tractions of Eq. (SBI) for u+-_{n+1};
+ *   (3) one traction on both faces, tau = S+ - z v+ = S- + z v- with
+ *       z = (mu/c_s)(1, c_p/c_s, 1), equal normal velocities (no opening or
+ *       interpenetration, Section 2.1), and stick/slip of the shear traction
+ *       vector against sigma^n mu(|delta|), sigma^n = sigma0 - tau_2 (Eq. (slipweak)):
+ *       V = v+ - v- = 2 (tau_stick - tau)/z_s with tau_stick = (S+ + S-)/2.
+ *   precision  any sbim_precision; fields are double for SBIM_FP64, else float
+ *   symmetric  1: the symmetry-plane reduction of Section 3 (the lower face is the
+ *              mirror image of the upper one, u-_1,3 = -u+_1,3 and u-_2 = u+_2, so
+ *              S-_1,3 = S+_1,3, S-_2 = -S+_2, and only the upper half-space is
+ *              evaluated: half the memory and time); 0: two half-spaces
+ * Fields u, v are [2][3][n3][n1] (face 0 upper, face 1 lower), perturbations
+ * from the prestressed equilibrium, starting at rest.  Without
+ * sbim_fault_set_fault the fault is welded (V = 0).
+ */
+int sbim_fault_create(sbim_fault* out, int n1, int n3, double L1, double L3, double cs,
+                      double cp, double rho, double dt, int n_cut, int precision, int symmetric,
+                      void* stream);
+
+/* sbim_fault_set_fault -- as sbim_hybrid_set_fault: HOST maps [n3][n1] of mu_s and
+ * the x1 shear prestress tau0 (Pa); mu_k, Dc (m), sigma0 (compression positive, Pa). */
+int sbim_fault_set_fault(sbim_fault h, const double* mu_s, const double* tau0, double mu_k,
+                         double Dc, double sigma0);
+
+/* sbim_fault_set_state / get_state -- device [2][3][n3][n1] displacement and
+ * velocity of the two faces (NULL: zero on set, skip on get).  The symmetric
+ * solver replaces the lower face by the mirror image of the upper one. */
+int sbim_fault_set_state(sbim_fault h, const void* u, const void* v);
+int sbim_fault_get_state(sbim_fault h, void* u, void* v);
+
+/* sbim_fault_step -- one time step, stream-ordered, no host sync. */
+int sbim_fault_step(sbim_fault h);
+
+/* sbim_fault_fields -- device outputs [3][n3][n1] (any may be NULL): slip u+ - u-,
+ * slip rate v+ - v- and fault traction perturbation of the last step (Pa). */
+int sbim_fault_fields(sbim_fault h, void* slip, void* slip_rate, void* traction);
+
+/* sbim_fault_info -- steps taken and the SBIM handles (lower is NULL when symmetric). */
+int sbim_fault_info(sbim_fault h, long long* steps, sbim_handle* upper, sbim_handle* lower);
+
+int sbim_fault_destroy(sbim_fault h);
+
+/* ------------------------------------------------------------------------- */
 /* Hybrid FEM-SBIM time step (Section 2.4) with an explicit FEM slab        */
 /* (Section 2.2) and a slip-weakening fault (Section 2.1).                   */
 /* ------------------------------------------------------------------------- */

@@ -54,6 +54,14 @@ def lib():
     L.sbim_check_device.argtypes = [vp]
     L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
+    L.sbim_fault_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, i, i, i, vp]
+    L.sbim_fault_set_fault.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), d, d, d]
+    L.sbim_fault_set_state.argtypes = [vp, vp, vp]
+    L.sbim_fault_get_state.argtypes = [vp, vp, vp]
+    L.sbim_fault_step.argtypes = [vp]
+    L.sbim_fault_fields.argtypes = [vp, vp, vp, vp]
+    L.sbim_fault_info.argtypes = [vp, ctypes.POINTER(ll), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.sbim_fault_destroy.argtypes = [vp]
     L.sbim_hybrid_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, d, d, d, i, i, i, i, vp]
     L.sbim_hybrid_set_fault.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), d, d, d]
     L.sbim_hybrid_set_state.argtypes = [vp, vp, vp, vp]
@@ -260,6 +268,44 @@ def sbim_hybrid_batch_replay(b):
 
 def sbim_hybrid_batch_destroy(b):
     _check(lib().sbim_hybrid_batch_destroy(b))
+
+
+def sbim_fault_create(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, precision, symmetric, stream):
+    hh = ctypes.c_void_p()
+    _check(lib().sbim_fault_create(ctypes.byref(hh), n1, n3, L1, L3, cs, cp, rho, dt, n_cut,
+                                   precision, symmetric, stream))
+    return hh
+
+
+def sbim_fault_set_fault(h, mu_s_ptr, tau0_ptr, mu_k, Dc, sigma0):
+    _check(lib().sbim_fault_set_fault(h, mu_s_ptr, tau0_ptr, mu_k, Dc, sigma0))
+
+
+def sbim_fault_set_state(h, u_ptr, v_ptr):
+    _check(lib().sbim_fault_set_state(h, u_ptr, v_ptr))
+
+
+def sbim_fault_get_state(h, u_ptr, v_ptr):
+    _check(lib().sbim_fault_get_state(h, u_ptr, v_ptr))
+
+
+def sbim_fault_step(h):
+    _check(lib().sbim_fault_step(h))
+
+
+def sbim_fault_fields(h, slip_ptr, rate_ptr, traction_ptr):
+    _check(lib().sbim_fault_fields(h, slip_ptr, rate_ptr, traction_ptr))
+
+
+def sbim_fault_info(h):
+    steps = ctypes.c_longlong()
+    up, lo = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().sbim_fault_info(h, ctypes.byref(steps), ctypes.byref(up), ctypes.byref(lo)))
+    return steps.value, up, lo
+
+
+def sbim_fault_destroy(h):
+    _check(lib().sbim_fault_destroy(h))
 
 
 def sbim_hybrid_create(n1, n2, n3, h, cs, cp, rho, dt, n_cut, precision, boundaries, fault,
