@@ -420,8 +420,10 @@ int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* t
  * sbim_hybrid_adjoint_step -- transpose of one step of the functional
  * sum_n <tau_n, tau_bar_n> of the fault tractions tau_n (Eqs. (fepred)-(fecorr),
  * (freeslip)-(stickslip), (slipweak), and the SBIM transposes).  h: a handle with
- * the same parameters and fault law, used only for this sweep (its SBIM half-spaces
- * take sbim_step_adjoint calls): call for steps N-1, ..., 0 in that order.
+ * the same parameters and fault law whose two SBIM half-spaces (sbim_hybrid_info)
+ * were reset before the sweep; they take the sbim_step_adjoint calls.  The call
+ * reads no FE state of h, so the same handle may recompute states with
+ * sbim_hybrid_step_given between calls.  Call for steps N-1, ..., 0 in that order.
  *   u, v, a           device, the state before step n  [L][3][n3][n1]
  *   tau_top, tau_bot  device, that step's boundary tractions [3][n3][n1]
  *   tau_bar           device, cotangent of the step's fault traction [3][n3][n1] (or NULL)

@@ -69,49 +69,44 @@ class HybridRupture(torch.autograd.Function):
         if dcv.ndim:
             raise ValueError("Dc must be a 0-d tensor (a uniform slip-weakening distance)")
         h = Hybrid(**params)
-        try:
-            h.set_fault(law["mu_s"], law["tau0"], law["mu_k"], float(dcv), law["sigma0"])
-            ckpt, ttop, tbot, taus = {}, [], [], []
-            for n in range(steps):
-                if n % every == 0:
-                    ckpt[n] = h.get_state()
-                h.step()
-                top, bot = h.boundary_tractions()
-                ttop.append(top)
-                tbot.append(bot)
-                taus.append(h.fault_fields()[2])
-        finally:
-            h.close()
+        h.set_fault(law["mu_s"], law["tau0"], law["mu_k"], float(dcv), law["sigma0"])
+        ckpt, ttop, tbot, taus = {}, [], [], []
+        for n in range(steps):
+            if n % every == 0:
+                ckpt[n] = h.get_state()
+            h.step()
+            top, bot = h.boundary_tractions()
+            ttop.append(top)
+            tbot.append(bot)
+            taus.append(h.fault_fields()[2])
+        # the handle is reused by the backward sweep: its FE state for the
+        # recomputation, its (reset) half-spaces for the SBIM transposes
+        ctx.h = h
         ctx.params, ctx.law, ctx.steps, ctx.every, ctx.dc = params, law, steps, every, float(dcv)
         ctx.ckpt, ctx.ttop, ctx.tbot = ckpt, ttop, tbot
         return torch.stack(taus)
 
     @staticmethod
     def backward(ctx, tau_bar):
-        from .hybrid import Hybrid
+        from . import sbim as B
         tau_bar = tau_bar.contiguous()
-        law = ctx.law
-        adj = Hybrid(**ctx.params)
-        rec = Hybrid(**ctx.params)
-        try:
-            for x in (adj, rec):
-                x.set_fault(law["mu_s"], law["tau0"], law["mu_k"], ctx.dc, law["sigma0"])
-            lu = torch.zeros(adj.shape, dtype=adj.dtype, device=tau_bar.device)
-            lv, la = torch.zeros_like(lu), torch.zeros_like(lu)
-            dcb = torch.zeros((adj.n3, adj.n1), dtype=adj.dtype, device=tau_bar.device)
-            for s0 in reversed(range(0, ctx.steps, ctx.every)):
-                s1 = min(s0 + ctx.every, ctx.steps)
-                rec.set_state(*ctx.ckpt[s0])
-                states = []
-                for n in range(s0, s1):
-                    states.append(rec.get_state())
-                    rec.step_given(ctx.ttop[n], ctx.tbot[n])
-                for n in range(s1 - 1, s0 - 1, -1):
-                    u, v, a = states[n - s0]
-                    adj.adjoint_step(u, v, a, ctx.ttop[n], ctx.tbot[n], tau_bar[n], lu, lv, la, dcb)
-        finally:
-            adj.close()
-            rec.close()
+        h = ctx.h
+        _, _, top, bot = B.sbim_hybrid_info(h.h)
+        B.sbim_reset(top)                  # the adjoint sweep starts from rest
+        B.sbim_reset(bot)
+        lu = torch.zeros(h.shape, dtype=h.dtype, device=tau_bar.device)
+        lv, la = torch.zeros_like(lu), torch.zeros_like(lu)
+        dcb = torch.zeros((h.n3, h.n1), dtype=h.dtype, device=tau_bar.device)
+        for s0 in reversed(range(0, ctx.steps, ctx.every)):
+            s1 = min(s0 + ctx.every, ctx.steps)
+            h.set_state(*ctx.ckpt[s0])
+            states = []
+            for n in range(s0, s1):
+                states.append(h.get_state())
+                h.step_given(ctx.ttop[n], ctx.tbot[n])
+            for n in range(s1 - 1, s0 - 1, -1):
+                u, v, a = states[n - s0]
+                h.adjoint_step(u, v, a, ctx.ttop[n], ctx.tbot[n], tau_bar[n], lu, lv, la, dcb)
         return dcb.sum().to(torch.float64), None, None, None, None
 
 
