@@ -133,6 +133,15 @@ int sbim_set_far_field(sbim_handle h, const double tau_inf[3]);
 /* sbim_reset -- forget the history; the next sbim_step is step 0 again. */
 int sbim_reset(sbim_handle h);
 
+/*
+ * sbim_rewind -- take back the last sbim_step (or sbim_step_adjoint): the step
+ * counter goes back by one and the next call evaluates the same time level again,
+ * overwriting that level's history entry.  This is what a predictor-corrector
+ * time stepper needs (evaluate at a predicted displacement, rewind, evaluate at the
+ * corrected one).  Stream-ordered; SBIM_ERR_STATE at step 0.
+ */
+int sbim_rewind(sbim_handle h);
+
 /* sbim_get_step -- number of sbim_step calls since creation or the last reset. */
 int sbim_get_step(sbim_handle h, long long* n);
 
@@ -306,15 +315,19 @@ typedef struct sbim_fault_ctx* sbim_fault;
 /*
  * sbim_fault_create -- a planar fault x2 = 0 between two identical elastic
  * half-spaces, each represented only by its boundary through Eq. (SBI) (an
- * upper, side +1, and a lower, side -1, sbim_handle of the given parameters; the
- * paper describes no steps for this solver, which are):
- *   (1) u+-_{n+1} = u+-_n + dt v+-_n on the two faces;
- *   (2) S+- = the non-local tractions of Eq. (SBI) for u+-_{n+1};
- *   (3) one traction on both faces, tau = S+ - z v+ = S- + z v- with
+ * upper, side +1, and a lower, side -1, sbim_handle of the given parameters).
+ * The paper describes no steps for this solver; each time step is the
+ * predictor-corrector of Lapusta et al. (2000): a solve at u* = u_n + dt v_n
+ * gives v*, the predictor's SBIM evaluation is withdrawn (sbim_rewind), and a
+ * solve at u_{n+1} = u_n + dt (v_n + v*)/2 gives v_{n+1}.  One solve at face
+ * displacements u+-:
+ *   (a) S+- = the non-local tractions of Eq. (SBI) for u+- (velocity 0);
+ *   (b) one traction on both faces, tau = S+ - z v+ = S- + z v- with
  *       z = (mu/c_s)(1, c_p/c_s, 1), equal normal velocities (no opening or
  *       interpenetration, Section 2.1), and stick/slip of the shear traction
  *       vector against sigma^n mu(|delta|), sigma^n = sigma0 - tau_2 (Eq. (slipweak)):
  *       V = v+ - v- = 2 (tau_stick - tau)/z_s with tau_stick = (S+ + S-)/2.
+ * Each step therefore evaluates each half-space twice.
  *   precision  any sbim_precision; fields are double for SBIM_FP64, else float
  *   symmetric  1: the symmetry-plane reduction of Section 3 (the lower face is the
  *              mirror image of the upper one, u-_1,3 = -u+_1,3 and u-_2 = u+_2, so

@@ -12,25 +12,31 @@ nonlinearity, so a boundary-only solver of this kind is the reference the paper
 checks the hybrid scheme against; the paper gives no steps for it, and these are
 written from Section 2.1's fault conditions and Eq. (SBI).
 
-Per step n -> n+1, with the two faces' displacements u+, u- and velocities:
-  1. u+-_{n+1} = u+-_n + dt v+-_n.
-  2. S+- = the non-local tractions of Eq. (SBI) of the upper (side +1) and lower
-     (side -1) half-spaces for u+-_{n+1} (radiation term left out: velocity 0).
-  3. The faces carry one traction tau = S+ - z v+ = S- + z v- (z_i = eta_i mu/c_s,
+Per step n -> n+1, with the two faces' displacements u+, u- and velocities v+-,
+the second-order predictor-corrector of Lapusta et al. (2000):
+  1. predictor u*+- = u+-_n + dt v+-_n; solve (below) -> v*+-;
+  2. corrector u+-_{n+1} = u+-_n + dt (v+-_n + v*+-)/2; the predictor's evaluation
+     is withdrawn from the half-spaces' histories and the solve is repeated at
+     u+-_{n+1} -> v+-_{n+1}.
+The solve at face displacements u+-:
+  a. S+- = the non-local tractions of Eq. (SBI) of the upper (side +1) and lower
+     (side -1) half-spaces for u+- (radiation term left out: velocity 0).
+  b. The faces carry one traction tau = S+ - z v+ = S- + z v- (z_i = eta_i mu/c_s,
      the radiation impedances of Eq. (SBI)); the normal velocities are equal (no
      opening, no interpenetration).  With V = v+ - v- and vbar = (v+ + v-)/2 this
      gives vbar = (S+ - S-)/(2z) and tau = tau_stick - z V/2, tau_stick = (S+ + S-)/2.
-  4. Stick/slip on the shear traction vector as in the hybrid scheme: the fault
+  c. Stick/slip on the shear traction vector as in the hybrid scheme: the fault
      sticks (V = 0) while |tau0 + tau_stick| <= sigma^n mu(|delta|),
      sigma^n = sigma0 - tau_stick_2, delta = u+ - u-; otherwise the shear traction
      is the strength along tau0 + tau_stick and V = 2 (tau_stick - tau)/z.
-  5. v+- = vbar +- V/2.
+  d. v+- = vbar +- V/2.
 
 Readings (the paper is silent):
-  * The displacement update of step 1 is the explicit one of spectral boundary
-    integral fault solvers (the new slip from the last slip rate), so each step
-    evaluates each half-space once; the velocity of step 3 enters only through
-    the radiation term, as in Eq. (SBI).
+  * The time stepping is Lapusta et al.'s predictor-corrector (two evaluations of
+    each half-space per step); the one-evaluation explicit update u_{n+1} = u_n +
+    dt v_n is unstable here: its highest modes (|k| c_s dt = 0.77 at
+    dt = 0.3 dx/c_p) grow without bound over a few hundred steps.  The velocity
+    enters Eq. (SBI) only through the radiation term, as in the paper.
   * ``symmetric=True`` is the paper's symmetry-plane reduction of TPV3
     (Section 3: only x2 > 0 is modelled, [u2] = 0 and sigma_22 constant): the
     lower face is the mirror image of the upper one (u-_1,3 = -u+_1,3,
@@ -79,21 +85,19 @@ class PureSBIMOracle:
     def slip(self):
         return self.u[0] - self.u[1]
 
-    def step(self):
-        dt, z, fl = self.dt, self.z, self.fault
-        u_new = self.u + dt * self.v                                   # step 1
-        if self.symmetric:
-            u_new[1] = self.mirror(u_new[0])
+    def _solve(self, u_new):
+        """Steps a-d at face displacements u_new: (v, traction, slip rate)."""
+        z, fl = self.z, self.fault
         zero = np.zeros((3, self.n3, self.n1))
-        s_up = self.up.step(u_new[0], zero)["s"]                       # step 2
+        s_up = self.up.step(u_new[0], zero)["s"]                       # step a
         if self.symmetric:                                             # mirror image
             s_lo = np.stack([s_up[0], -s_up[1], s_up[2]])
         else:
             s_lo = self.lo.step(u_new[1], zero)["s"]
-        stick = 0.5 * (s_up + s_lo)                                    # step 3
+        stick = 0.5 * (s_up + s_lo)                                    # step b
         vbar = (s_up - s_lo) / (2.0 * z)
         tau = stick.copy()
-        if fl is not None:                                             # step 4
+        if fl is not None:                                             # step c
             d = u_new[0] - u_new[1]
             slip = np.hypot(d[0], d[2])
             strength = (fl.sigma0 - stick[1]) * fl.friction(slip)
@@ -106,8 +110,23 @@ class PureSBIMOracle:
         V = np.zeros_like(stick)
         V[0] = 2.0 * (stick[0] - tau[0]) / z[0]
         V[2] = 2.0 * (stick[2] - tau[2]) / z[2]
-        self.v = np.stack([vbar + 0.5 * V, vbar - 0.5 * V])            # step 5
+        return np.stack([vbar + 0.5 * V, vbar - 0.5 * V]), tau, V       # step d
+
+    def _mirrored(self, u):
+        if self.symmetric:
+            u = u.copy()
+            u[1] = self.mirror(u[0])
+        return u
+
+    def step(self):
+        dt = self.dt
+        u_pred = self._mirrored(self.u + dt * self.v)                  # predictor
+        v_pred, _, _ = self._solve(u_pred)
+        self.up.rewind()
+        if self.lo is not None:
+            self.lo.rewind()
+        u_new = self._mirrored(self.u + 0.5 * dt * (self.v + v_pred))  # corrector
+        self.v, self.fault_traction, self.slip_rate = self._solve(u_new)
         self.u = u_new
-        self.fault_traction, self.slip_rate = tau, V
         self.n += 1
-        return tau
+        return self.fault_traction

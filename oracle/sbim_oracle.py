@@ -464,6 +464,14 @@ class SBIMOracle:
         self.n += 1
         return {"tau": tau, "s": s, "F": F, "imag": imag}
 
+    def rewind(self):
+        """Forget the last step (its displacement leaves the history), so that
+        the next ``step`` evaluates the same time level again."""
+        if self.n == 0:
+            raise ValueError("nothing to rewind")
+        self.history.pop()
+        self.n -= 1
+
 
 # ---------------------------------------------------------------------------
 # Adjoint (transpose) of a sequence of traction updates, built as the literal

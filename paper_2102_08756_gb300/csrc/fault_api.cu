@@ -3,13 +3,18 @@
 // only by its boundary through Eq. (SBI).  The TPV3 benchmark of Section 3 has
 // no off-fault nonlinearity, so this boundary-only solver is the reference the
 // hybrid scheme is checked against.  One sbim_fault_step enqueues on the
-// handle's stream:
-//   (1) u+-_{n+1} = u+-_n + dt v+-_n                          (predict_kernel)
-//   (2) the non-local tractions S+- of the upper (side +1) and lower (side -1)
-//       half-spaces for u+-_{n+1}, radiation term left out     (sbim_step x 2)
-//   (3) one traction on both faces, tau = S+ - z v+ = S- + z v-, equal normal
-//       velocities, stick/slip on the shear vector, v+- = vbar +- V/2
-//                                                              (solve_kernel)
+// handle's stream the predictor-corrector of Lapusta et al. (2000):
+//   (1) u* = u_n + dt v_n                                      (predict_kernel)
+//   (2) solve at u* -> v*                                      (solve, below)
+//   (3) withdraw the predictor's evaluation                    (sbim_rewind)
+//   (4) u_{n+1} = u_n + dt (v_n + v*)/2                        (correct_kernel)
+//   (5) solve at u_{n+1} -> v_{n+1}
+// where one solve is: the non-local tractions S+- of the upper (side +1) and
+// lower (side -1) half-spaces, radiation term left out (sbim_step x 2), then
+// one traction on both faces, tau = S+ - z v+ = S- + z v-, equal normal
+// velocities, stick/slip on the shear vector, v+- = vbar +- V/2 (solve_kernel).
+// The one-evaluation explicit update u_{n+1} = u_n + dt v_n is unstable at the
+// highest modes; the corrector makes the scheme stable and second order.
 // With symmetric = 1 (the symmetry-plane reduction used for TPV3 in Section 3)
 // the lower face is the mirror image of the upper one and only the upper
 // half-space is evaluated: S-_1,3 = S+_1,3, S-_2 = -S+_2.
@@ -27,6 +32,8 @@ struct sbim_fault_ctx {
   sbim_handle up = nullptr, lo = nullptr;
   void* u = nullptr;         // [2][3][n3][n1]: face 0 upper (+), face 1 lower (-)
   void* v = nullptr;
+  void* u_pred = nullptr;    // [2][3][n3][n1] predictor displacement
+  void* v_pred = nullptr;    // [2][3][n3][n1] predictor velocity
   void* s_up = nullptr;      // [3][n3][n1] non-local tractions
   void* s_lo = nullptr;
   void* zero = nullptr;      // [3][n3][n1] zero velocity for the SBIM calls
@@ -69,17 +76,31 @@ __device__ __forceinline__ R mirror(R x, int c) {
   return c == 1 ? x : -x;
 }
 
-// Step (1): explicit displacement update; the symmetric solver keeps the lower
-// face at the mirror image of the upper one.
+// Step (1): u* = u + dt v; the symmetric solver keeps the lower face at the
+// mirror image of the upper one.
 template <class R, bool SYM>
-__global__ void predict_kernel(R* __restrict__ u, const R* __restrict__ v, long long plane, R dt) {
+__global__ void predict_kernel(const R* __restrict__ u, const R* __restrict__ v,
+                               R* __restrict__ out, long long plane, R dt) {
   const long long face = 3 * plane;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < face;
        i += (long long)gridDim.x * blockDim.x) {
     const R up = u[i] + dt * v[i];
+    out[i] = up;
+    out[face + i] = SYM ? mirror(up, (int)(i / plane)) : u[face + i] + dt * v[face + i];
+  }
+}
+
+// Step (4): u += dt (v + v*)/2, in place.
+template <class R, bool SYM>
+__global__ void correct_kernel(R* __restrict__ u, const R* __restrict__ v,
+                               const R* __restrict__ vp, long long plane, R dt) {
+  const long long face = 3 * plane;
+  const R h = (R)0.5 * dt;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < face;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R up = u[i] + h * (v[i] + vp[i]);
     u[i] = up;
-    if (SYM) u[face + i] = mirror(up, (int)(i / plane));
-    else u[face + i] += dt * v[face + i];
+    u[face + i] = SYM ? mirror(up, (int)(i / plane)) : u[face + i] + h * (v[face + i] + vp[face + i]);
   }
 }
 
@@ -91,7 +112,7 @@ struct Law {
   int weld;
 };
 
-// Step (3) at one fault node: traction continuity through the radiation
+// The solve at one fault node: traction continuity through the radiation
 // impedances z = (mu/c_s)(1, c_p/c_s, 1), stick/slip on the shear vector.
 template <class R, bool SYM>
 __global__ void solve_kernel(const R* __restrict__ u, R* __restrict__ v, const R* __restrict__ s_up,
@@ -163,19 +184,16 @@ void release(sbim_fault_ctx* c) {
   if (!c) return;
   sbim_destroy(c->up);
   sbim_destroy(c->lo);
-  for (void* p : {c->u, c->v, c->s_up, c->s_lo, c->zero, c->mu_s, c->tau0, c->traction, c->rate})
+  for (void* p : {c->u, c->v, c->u_pred, c->v_pred, c->s_up, c->s_lo, c->zero, c->mu_s, c->tau0, c->traction, c->rate})
     if (p) cudaFree(p);
   delete c;
 }
 
+// One solve at face displacements u: the two SBIM evaluations, then the
+// traction-continuity / stick-slip kernel writing the face velocities to v_out.
 template <class R>
-int step_impl(sbim_fault_ctx* h) {
+int solve(sbim_fault_ctx* h, const R* u, R* v_out) {
   const long long np = h->plane();
-  const R dt = (R)h->dt;
-  R* u = (R*)h->u;
-  if (h->symmetric) predict_kernel<R, true><<<grid_for(3 * np), kThreads, 0, h->stream>>>(u, (const R*)h->v, np, dt);
-  else predict_kernel<R, false><<<grid_for(3 * np), kThreads, 0, h->stream>>>(u, (const R*)h->v, np, dt);
-  FCU(cudaGetLastError());
   const size_t face = 3 * (size_t)np;
   int rc = sbim_step(h->up, u, h->zero, h->s_up);
   if (rc != SBIM_OK) return rc;
@@ -189,14 +207,39 @@ int step_impl(sbim_fault_ctx* h) {
              h->have_law ? 0 : 1};
   const int blocks = (int)((np + kThreads - 1) / kThreads);
   if (h->symmetric)
-    solve_kernel<R, true><<<blocks, kThreads, 0, h->stream>>>(u, (R*)h->v, (const R*)h->s_up, nullptr,
+    solve_kernel<R, true><<<blocks, kThreads, 0, h->stream>>>(u, v_out, (const R*)h->s_up, nullptr,
                                                               (R*)h->traction, (R*)h->rate, law, np,
                                                               z_s, z_p);
   else
     solve_kernel<R, false><<<blocks, kThreads, 0, h->stream>>>(
-        u, (R*)h->v, (const R*)h->s_up, (const R*)h->s_lo, (R*)h->traction, (R*)h->rate, law, np,
+        u, v_out, (const R*)h->s_up, (const R*)h->s_lo, (R*)h->traction, (R*)h->rate, law, np,
         z_s, z_p);
   FCU(cudaGetLastError());
+  return SBIM_OK;
+}
+
+template <class R>
+int step_impl(sbim_fault_ctx* h) {
+  const long long np = h->plane();
+  const R dt = (R)h->dt;
+  R* u = (R*)h->u;
+  R* v = (R*)h->v;
+  R* up = (R*)h->u_pred;
+  R* vp = (R*)h->v_pred;
+  const int g = grid_for(3 * np);
+  if (h->symmetric) predict_kernel<R, true><<<g, kThreads, 0, h->stream>>>(u, v, up, np, dt);
+  else predict_kernel<R, false><<<g, kThreads, 0, h->stream>>>(u, v, up, np, dt);
+  FCU(cudaGetLastError());
+  int rc = solve<R>(h, up, vp);
+  if (rc != SBIM_OK) return rc;
+  rc = sbim_rewind(h->up);
+  if (rc == SBIM_OK && h->lo) rc = sbim_rewind(h->lo);
+  if (rc != SBIM_OK) return rc;
+  if (h->symmetric) correct_kernel<R, true><<<g, kThreads, 0, h->stream>>>(u, v, vp, np, dt);
+  else correct_kernel<R, false><<<g, kThreads, 0, h->stream>>>(u, v, vp, np, dt);
+  FCU(cudaGetLastError());
+  rc = solve<R>(h, u, v);
+  if (rc != SBIM_OK) return rc;
   ++h->n;
   return SBIM_OK;
 }
@@ -225,7 +268,7 @@ int sbim_fault_create(sbim_fault* out, int n1, int n3, double L1, double L3, dou
     else if (cudaMemsetAsync(*p, 0, bytes, c->stream) != cudaSuccess) rc = ffail(SBIM_ERR_CUDA, "memset");
   };
   const size_t pb = 3 * c->plane() * c->rs;
-  alloc(&c->u, 2 * pb); alloc(&c->v, 2 * pb);
+  alloc(&c->u, 2 * pb); alloc(&c->v, 2 * pb); alloc(&c->u_pred, 2 * pb); alloc(&c->v_pred, 2 * pb);
   alloc(&c->s_up, pb); alloc(&c->zero, pb); alloc(&c->traction, pb); alloc(&c->rate, pb);
   if (!c->symmetric) alloc(&c->s_lo, pb);
   alloc(&c->mu_s, c->plane() * c->rs); alloc(&c->tau0, c->plane() * c->rs);

@@ -704,6 +704,14 @@ int sbim_reset(sbim_handle h) {
   return SBIM_OK;
 }
 
+int sbim_rewind(sbim_handle h) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (h->n == 0) return fail(SBIM_ERR_STATE, "no step to rewind");
+  CU(sbim::launch_rewind(h->d_step, h->stream));
+  --h->n;
+  return SBIM_OK;
+}
+
 int sbim_get_step(sbim_handle h, long long* n) {
   if (!h || !n) return fail(SBIM_ERR_ARG, "NULL argument");
   *n = h->n;

@@ -228,6 +228,11 @@ __global__ void adjoint_epilogue_kernel(const R* __restrict__ tau_bar, R* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
 }
 
+// Step counter one back (sbim_rewind): the next step rewrites the same ring slot.
+__global__ void rewind_kernel(long long* step) {
+  if (threadIdx.x == 0 && *step > 0) *step -= 1;
+}
+
 template <class S, int KAHAN>
 cudaError_t conv_dispatch(const StepArgs& a, cudaStream_t st) {
   const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
@@ -313,6 +318,11 @@ cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, v
         (float)coef[1], (float)coef[2], (float)tau_inf[0], (float)tau_inf[1],
         (float)tau_inf[2], step);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rewind(long long* step, cudaStream_t st) {
+  rewind_kernel<<<1, 32, 0, st>>>(step);
   return cudaGetLastError();
 }
 

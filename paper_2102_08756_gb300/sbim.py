@@ -43,6 +43,7 @@ def lib():
     L.sbim_step_adjoint.argtypes = [vp, vp, vp, vp]
     L.sbim_set_far_field.argtypes = [vp, ctypes.POINTER(d)]
     L.sbim_reset.argtypes = [vp]
+    L.sbim_rewind.argtypes = [vp]
     L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
     L.sbim_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -136,6 +137,10 @@ def sbim_set_far_field(h, tau_inf):
 
 def sbim_reset(h):
     _check(lib().sbim_reset(h))
+
+
+def sbim_rewind(h):
+    _check(lib().sbim_rewind(h))
 
 
 def sbim_get_step(h):
@@ -435,6 +440,9 @@ class SBIM:
 
     def reset(self):
         sbim_reset(self.h)
+
+    def rewind(self):
+        sbim_rewind(self.h)
 
     @property
     def n(self):

@@ -1,6 +1,7 @@
 """Checkpoint and restore of an SBIM handle (sbim_save / sbim_load): the state of
 the truncated convolution of Eq. (SBI) is the step counter and the history ring;
-a run restored from a checkpoint must continue bit-for-bit."""
+a run restored from a checkpoint must continue bit-for-bit.  sbim_rewind takes
+back one step: the next step re-evaluates that level."""
 import numpy as np
 import pytest
 
@@ -81,3 +82,25 @@ def test_load_rejects_other_parameters_and_garbage():
     with pytest.raises(SBIMError):
         sbim._check(sbim.lib().sbim_save(a.h, small.ctypes.data, ctypes.byref(cap)))
     assert cap.value == need.value
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_rewind_reevaluates_the_level(precision):
+    from paper_2102_08756_gb300.sbim import SBIMError
+    n1, n3, n_cut = 16, 12, 6
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    g = torch.Generator().manual_seed(2)
+    x = [torch.randn((3, n3, n1), generator=g, dtype=torch.float64).to("cuda", tdt) * 1e-3
+         for _ in range(10)]
+    a = _make(n1, n3, n_cut, precision)
+    b = _make(n1, n3, n_cut, precision)
+    with pytest.raises(SBIMError):
+        a.rewind()
+    for m in range(8):                     # past the cutoff: the ring has wrapped
+        a.step(x[m], x[m + 1])
+        b.step(x[m], x[m + 1])
+    a.step(x[9], x[0])
+    a.rewind()
+    assert a.n == 8
+    assert torch.equal(a.step(x[0], x[1]), b.step(x[0], x[1]))
+    assert torch.equal(a.step(x[2], x[3]), b.step(x[2], x[3]))

@@ -4,12 +4,15 @@ the mathematics and the paper fix, not against itself:
 * a spatially uniform overstressed fault slides at the rate set by the two
   radiation impedances, V = 2 c_s (tau0 - tau_f)/mu, from its first step (the
   k = 0 mode has no non-local term, Section 2.3);
-* a frictionless fault under a sinusoidal prestress converges, as dt -> 0, to
-  the continuum solution of the two-half-space problem: for slip normal to the
-  wavevector (mode III) delta(t) = (2 A/(mu k)) int_0^{k c_s t} J0, and for slip
-  along it (mode II) the inverse Laplace transform of 2 A/(mu k p M(p)),
-  M = K11 - G^2/K22 (the normal displacement adjusts so sigma_22 stays
-  continuous), computed by fixed-Talbot inversion (Abate & Valko 2004);
+* a frictionless fault under a sinusoidal prestress converges at second order
+  in dt to the continuum solution of the two-half-space problem: for slip
+  normal to the wavevector (mode III) delta(t) = (2 A/(mu k)) int_0^{k c_s t} J0,
+  and for slip along it (mode II) the inverse Laplace transform of
+  2 A/(mu k p M(p)), M = K11 - G^2/K22 (the normal displacement adjusts so
+  sigma_22 stays continuous), computed by fixed-Talbot inversion (Abate &
+  Valko 2004);
+* the predictor-corrector stays bounded at the highest modes, where the
+  one-evaluation explicit update grows without bound;
 * the symmetry-plane reduction of Section 3 equals the two-half-space solver on
   a symmetric problem, and the normal traction does not change;
 * the paper's validation of the hybrid scheme (Section 3): a rupture computed by
@@ -38,12 +41,13 @@ def test_uniform_overstress_slides_at_radiation_rate():
     V = 2.0 * CS * (tau0 - mu_f * sigma0) / MU
     for sym in (False, True):
         o = PureSBIMOracle(n1, n3, n1 * DX, n3 * DX, CS, CP, RHO, DT, 16, fl, symmetric=sym)
-        for n in range(12):
+        for n in range(1, 13):
             o.step()
             np.testing.assert_allclose(o.slip_rate[0], V, rtol=1e-12)
             np.testing.assert_allclose(o.slip_rate[2], 0.0, atol=1e-12 * V)
             np.testing.assert_allclose(o.fault_traction[0], mu_f * sigma0 - tau0, rtol=1e-12)
-            np.testing.assert_allclose(o.slip[0], n * DT * V, rtol=1e-12, atol=1e-15)
+            # trapezoidal slip from rest: the rate jumps to V in the first step
+            np.testing.assert_allclose(o.slip[0], (n - 0.5) * DT * V, rtol=1e-12, atol=1e-15)
             np.testing.assert_allclose(o.u[0, 0], -o.u[1, 0], rtol=1e-12)
 
 
@@ -58,18 +62,17 @@ def _frictionless_slip(n1, n3, tau0, dt, T_end, k, station):
     return np.array(out)
 
 
-def _richardson_errors(n1, n3, tau0, k, station, exact, T_end):
-    """Errors of the runs at dt, dt/2, dt/4 and of the Richardson combinations,
-    compared at t_n = n dt (the solution at step n is the response at t_{n-1}:
-    the prestress acts from the first step)."""
-    runs = [_frictionless_slip(n1, n3, tau0, DT / f, T_end, k, station) for f in (1, 2, 4)]
-    a = runs[0]
-    b = runs[1][0::2][:len(a)]
-    c = runs[2][0::4][:len(a)]
-    ts = np.arange(len(a)) * DT
-    ex = np.array([exact(k * CS * t) for t in ts])
-    err = lambda x: np.abs(x - ex).max()  # noqa: E731
-    return err(a), err(b), err(c), err(2 * b - a), err(2 * c - b)
+def _errors(n1, n3, tau0, k, station, exact, T_end):
+    """Max error of the runs at dt, dt/2, dt/4, each compared with the continuum
+    solution at t_n - dt/2 (trapezoidal start from rest: the prestress acts
+    from the first step, whose slip rate jumps to its full value)."""
+    out = []
+    for f in (1, 2, 4):
+        h = DT / f
+        x = _frictionless_slip(n1, n3, tau0, h, T_end, k, station)
+        ts = (np.arange(len(x)) + 0.5) * h
+        out.append(np.abs(x - np.array([exact(k * CS * t) for t in ts])).max())
+    return out
 
 
 def _talbot(F, t, M=48):
@@ -91,9 +94,9 @@ def test_mode_iii_converges_to_closed_form():
     tau0 = A * np.cos(k * x3)[:, None] * np.ones((n3, n1))      # x1 shear varying along x3
     scale = 2 * A / (MU * k)
     exact = lambda T: scale * quad(sp.j0, 0.0, T, limit=200)[0]  # noqa: E731
-    e1, e2, e4, r12, r24 = _richardson_errors(n1, n3, tau0, k, (0, 0), exact, 12.0)
-    assert e1 < 0.04 * scale and 1.8 < e1 / e2 < 2.2 and 1.8 < e2 / e4 < 2.2   # first order
-    assert r24 < 5e-4 * scale and r12 / r24 > 3.0                              # second-order remainder
+    e1, e2, e4 = _errors(n1, n3, tau0, k, (0, 0), exact, 12.0)
+    assert e1 < 1e-3 * scale and e4 < 5e-5 * scale
+    assert 3.5 < e1 / e2 < 4.5 and 3.5 < e2 / e4 < 4.5        # second order
 
 
 def test_mode_ii_converges_to_laplace_inversion():
@@ -115,12 +118,32 @@ def test_mode_ii_converges_to_laplace_inversion():
         F3 = lambda p: 1.0 / (p * laplace_symbols(p, eta)[2])  # noqa: E731
         assert abs(_talbot(F3, T) - quad(sp.j0, 0.0, T, limit=200)[0]) < 1e-7
     exact = lambda T: 0.0 if T == 0 else scale * _talbot(F, T)  # noqa: E731
-    e1, e2, e4, r12, r24 = _richardson_errors(n1, n3, tau0, k, (0, 0), exact, 10.0)
-    assert e1 < 0.05 * scale and 1.8 < e1 / e2 < 2.2 and 1.8 < e2 / e4 < 2.2
-    assert r24 < 8e-4 * scale and r12 / r24 > 3.0
+    e1, e2, e4 = _errors(n1, n3, tau0, k, (0, 0), exact, 10.0)
+    assert e1 < 2e-3 * scale and e4 < 1e-4 * scale
+    assert 3.5 < e1 / e2 < 4.5 and 3.5 < e2 / e4 < 4.5
     # the static limit 1/M(0) = 1/(2 (1 - c_s^2/c_p^2)) is the plane-strain
     # compliance 1 - nu: the time average of the response approaches it
     assert abs(1.0 / (F(np.array([1e-9 + 0j]))[0] * 1e-9) - 2 * (1 - 1 / eta ** 2)) < 1e-6
+
+
+def test_highest_modes_stay_bounded():
+    """Frictionless fault, random prestress on a 4 x 4 grid (every mode at or
+    near the Nyquist limit, |k| c_s dt up to 0.77): the slip rate stays at its
+    first-step size over 1500 steps."""
+    n = 4
+    rng = np.random.default_rng(0)
+    tau0 = rng.normal(size=(n, n)) * 1e6
+    tau0 -= tau0.mean()
+    fl = FaultLaw(np.zeros((n, n)), 0.0, 0.4, tau0, 1e8)
+    for sym in (True, False):
+        o = PureSBIMOracle(n, n, n * DX, n * DX, CS, CP, RHO, DT, 1501, fl, symmetric=sym)
+        o.step()
+        first = np.abs(o.slip_rate).max()
+        peak = 0.0
+        for _ in range(1499):
+            o.step()
+            peak = max(peak, np.abs(o.slip_rate).max())
+        assert peak < 2.0 * first, (peak, first)
 
 
 def _tpv3_like(n, half, Dc, mu_s_out=0.677):
@@ -177,5 +200,5 @@ def test_rupture_agrees_with_hybrid_and_converges():
     rms32, slip32, agree32 = _arrivals_and_slip(32, 6, 0.16, 80)
     rms64, slip64, agree64 = _arrivals_and_slip(64, 12, 0.32, 150)
     assert agree32 > 0.85 and agree64 > 0.95
-    assert rms64 < 0.04 and slip64 < 0.03
-    assert slip64 < 0.5 * slip32 and rms64 < rms32
+    assert rms64 < 0.06 and slip64 < 0.03
+    assert slip64 < 0.5 * slip32 and rms64 < 0.5 * rms32

@@ -183,3 +183,22 @@ def test_truncation_window_keeps_the_early_lags():
             np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.max(np.abs(a)))
         else:
             assert np.max(np.abs(b)) < 1e-9 * np.max(np.abs(a)) + 1e-300
+
+
+def test_rewind_evaluates_the_same_level_again():
+    """``rewind`` withdraws the last step: stepping a, rewinding and stepping b
+    gives what a handle that only ever saw b at that level gives."""
+    rng = np.random.default_rng(11)
+    args = (8, 6, 800.0, 600.0, 3464.0, 6000.0, 2670.0, 0.005, 5, 1)
+    x = [rng.normal(size=(3, 6, 8)) for _ in range(9)]
+    a = SBIMOracle(*args)
+    b = SBIMOracle(*args)
+    for m in range(7):
+        a.step(x[m], x[m + 1])
+        b.step(x[m], x[m + 1])
+    a.step(x[8], x[0])
+    a.rewind()
+    assert a.n == 7
+    ra = a.step(x[0], x[1])["tau"]
+    rb = b.step(x[0], x[1])["tau"]
+    assert np.array_equal(ra, rb)
