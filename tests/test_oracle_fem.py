@@ -2,8 +2,9 @@
 element stiffness against closed-form strain energies and rigid-body modes,
 mass conservation, energy conservation of free vibration, a welded split plane
 against the unsplit mesh, the linear slip-weakening law, a pulse that leaves
-through the SBIM boundaries without reflection, and independence of the fault
-solution from the strip width (the paper's own validation)."""
+through the SBIM boundaries without reflection, independence of the fault
+solution from the strip width (the paper's own validation), and the energy
+balance of a coupled rupture."""
 import numpy as np
 import pytest
 
@@ -159,3 +160,47 @@ def test_fault_solution_independent_of_strip_width():
     b = _rupture(8)
     assert np.max(np.abs(a)) > 1.0            # the rupture reached the station
     assert np.max(np.abs(a - b)) < 0.1 * np.max(np.abs(a)), np.max(np.abs(a - b)) / np.max(np.abs(a))
+
+
+def test_coupled_energy_balance():
+    """A short coupled rupture (Section 2.4): the slab's kinetic + strain energy
+    change equals the work of the SBIM boundary forces plus the work of the fault
+    tractions, within the central-difference time-integration error; the
+    half-spaces only absorb energy (radiated energy >= 0), and the work of the
+    initial shear stress exceeds the fault's net work by the frictional
+    dissipation, which is >= 0."""
+    n1 = n3 = 24
+    h = 100.0
+    dt = 0.3 * h / CP
+    steps = 60
+    i3, i1 = np.meshgrid(np.arange(n3), np.arange(n1), indexing="ij")
+    patch = (np.abs(i1 - n1 / 2 + 0.5) < 4) & (np.abs(i3 - n3 / 2 + 0.5) < 4)
+    tau0 = np.where(patch, 1.005 * 0.677 * 120e6, 70e6)
+    fl = FaultLaw(np.full((n3, n1), 0.677), 0.525, 0.08, tau0, 120e6)
+    me = SlabMesh(n1, 4, n3, h, fault=True)
+    o = HybridOracle(me, CS, CP, RHO, dt, n_cut=steps + 1, fault=fl)
+    A = h * h
+    p, q = me.f + 1, me.f
+    E0 = sum(o.energy())
+    w_sbim = w_fault = w_tau0 = 0.0
+    prev = (np.zeros_like(o.u), np.zeros_like(o.u))
+    for n in range(steps):
+        u0 = o.u.copy()
+        o.step()
+        du = o.u - u0
+        fs = np.zeros_like(o.u)
+        fs[me.top] += A * o.last_tau_top
+        fs[0] -= A * o.last_tau_bot
+        ff = np.zeros_like(o.u)
+        ff[p] -= A * o.fault_traction
+        ff[q] += A * o.fault_traction
+        w_sbim += np.sum(0.5 * (fs + prev[0]) * du)       # trapezoid in time
+        w_fault += np.sum(0.5 * (ff + prev[1]) * du)
+        w_tau0 += A * np.sum(fl.tau0 * (du[p, 0] - du[q, 0]))
+        prev = (fs, ff)
+        dE = sum(o.energy()) - E0
+        assert w_sbim <= 0.0                                # energy leaves into the half-spaces
+        assert w_tau0 - w_fault >= 0.0                      # friction dissipates
+        if n >= 24:                                         # past the start-up transient
+            assert abs(dE - w_sbim - w_fault) < 3e-3 * max(abs(dE), abs(w_fault)), n
+    assert -w_sbim > 0.3 * dE > 0                           # a real share is radiated
