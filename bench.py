@@ -471,10 +471,12 @@ def run_coupled(args):
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         time.sleep(0.3)
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(K):
             g.step()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
     slip, rate, _ = g.fault_fields()

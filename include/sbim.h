@@ -134,6 +134,19 @@ int sbim_set_far_field(sbim_handle h, const double tau_inf[3]);
 int sbim_reset(sbim_handle h);
 
 /*
+ * sbim_step_repeat -- evaluate the level of the last sbim_step again with a new
+ * displacement u and velocity v; the result equals sbim_rewind followed by
+ * sbim_step(u, v, tau) up to rounding.  Every lag >= 1 of the truncated
+ * convolution of Eq. (SBI) is unchanged, so only the lag-0 term, the assembly and
+ * the two plane FFTs are recomputed: a predictor-corrector time stepper pays for
+ * one history pass per step instead of two.  Needs a preceding sbim_step (or
+ * sbim_step_repeat) on this handle with no sbim_step_adjoint, sbim_rewind,
+ * sbim_reset, sbim_load, sbim_set_conv_config, sbim_set_window or batched step in
+ * between (SBIM_ERR_STATE otherwise).  Arguments as sbim_step; stream-ordered.
+ */
+int sbim_step_repeat(sbim_handle h, const void* u, const void* v, void* tau);
+
+/*
  * sbim_rewind -- take back the last sbim_step (or sbim_step_adjoint): the step
  * counter goes back by one and the next call evaluates the same time level again,
  * overwriting that level's history entry.  This is what a predictor-corrector
@@ -318,16 +331,16 @@ typedef struct sbim_fault_ctx* sbim_fault;
  * upper, side +1, and a lower, side -1, sbim_handle of the given parameters).
  * The paper describes no steps for this solver; each time step is the
  * predictor-corrector of Lapusta et al. (2000): a solve at u* = u_n + dt v_n
- * gives v*, the predictor's SBIM evaluation is withdrawn (sbim_rewind), and a
- * solve at u_{n+1} = u_n + dt (v_n + v*)/2 gives v_{n+1}.  One solve at face
- * displacements u+-:
+ * gives v*, and a solve at u_{n+1} = u_n + dt (v_n + v*)/2 gives v_{n+1}; the
+ * corrector's SBIM evaluation re-evaluates the predictor's level
+ * (sbim_step_repeat), so each step makes one pass over each history.  One solve
+ * at face displacements u+-:
  *   (a) S+- = the non-local tractions of Eq. (SBI) for u+- (velocity 0);
  *   (b) one traction on both faces, tau = S+ - z v+ = S- + z v- with
  *       z = (mu/c_s)(1, c_p/c_s, 1), equal normal velocities (no opening or
  *       interpenetration, Section 2.1), and stick/slip of the shear traction
  *       vector against sigma^n mu(|delta|), sigma^n = sigma0 - tau_2 (Eq. (slipweak)):
  *       V = v+ - v- = 2 (tau_stick - tau)/z_s with tau_stick = (S+ + S-)/2.
- * Each step therefore evaluates each half-space twice.
  *   precision  any sbim_precision; fields are double for SBIM_FP64, else float
  *   symmetric  1: the symmetry-plane reduction of Section 3 (the lower face is the
  *              mirror image of the upper one, u-_1,3 = -u+_1,3 and u-_2 = u+_2, so

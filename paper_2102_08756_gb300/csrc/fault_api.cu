@@ -6,9 +6,9 @@
 // handle's stream the predictor-corrector of Lapusta et al. (2000):
 //   (1) u* = u_n + dt v_n                                      (predict_kernel)
 //   (2) solve at u* -> v*                                      (solve, below)
-//   (3) withdraw the predictor's evaluation                    (sbim_rewind)
-//   (4) u_{n+1} = u_n + dt (v_n + v*)/2                        (correct_kernel)
-//   (5) solve at u_{n+1} -> v_{n+1}
+//   (3) u_{n+1} = u_n + dt (v_n + v*)/2                        (correct_kernel)
+//   (4) solve at u_{n+1} -> v_{n+1}, re-evaluating the predictor's level: the
+//       history sums over lags >= 1 are the predictor's (sbim_step_repeat)
 // where one solve is: the non-local tractions S+- of the upper (side +1) and
 // lower (side -1) half-spaces, radiation term left out (sbim_step x 2), then
 // one traction on both faces, tau = S+ - z v+ = S- + z v-, equal normal
@@ -90,7 +90,7 @@ __global__ void predict_kernel(const R* __restrict__ u, const R* __restrict__ v,
   }
 }
 
-// Step (4): u += dt (v + v*)/2, in place.
+// Step (3): u += dt (v + v*)/2, in place.
 template <class R, bool SYM>
 __global__ void correct_kernel(R* __restrict__ u, const R* __restrict__ v,
                                const R* __restrict__ vp, long long plane, R dt) {
@@ -189,16 +189,18 @@ void release(sbim_fault_ctx* c) {
   delete c;
 }
 
-// One solve at face displacements u: the two SBIM evaluations, then the
+// One solve at face displacements u: the SBIM evaluations (the corrector's
+// re-evaluates the predictor's level, reusing its history sums), then the
 // traction-continuity / stick-slip kernel writing the face velocities to v_out.
 template <class R>
-int solve(sbim_fault_ctx* h, const R* u, R* v_out) {
+int solve(sbim_fault_ctx* h, const R* u, R* v_out, bool again) {
   const long long np = h->plane();
   const size_t face = 3 * (size_t)np;
-  int rc = sbim_step(h->up, u, h->zero, h->s_up);
+  auto eval = again ? sbim_step_repeat : sbim_step;
+  int rc = eval(h->up, u, h->zero, h->s_up);
   if (rc != SBIM_OK) return rc;
   if (!h->symmetric) {
-    rc = sbim_step(h->lo, u + face, h->zero, h->s_lo);
+    rc = eval(h->lo, u + face, h->zero, h->s_lo);
     if (rc != SBIM_OK) return rc;
   }
   const R mu = (R)(h->rho * h->cs * h->cs);
@@ -230,15 +232,12 @@ int step_impl(sbim_fault_ctx* h) {
   if (h->symmetric) predict_kernel<R, true><<<g, kThreads, 0, h->stream>>>(u, v, up, np, dt);
   else predict_kernel<R, false><<<g, kThreads, 0, h->stream>>>(u, v, up, np, dt);
   FCU(cudaGetLastError());
-  int rc = solve<R>(h, up, vp);
-  if (rc != SBIM_OK) return rc;
-  rc = sbim_rewind(h->up);
-  if (rc == SBIM_OK && h->lo) rc = sbim_rewind(h->lo);
+  int rc = solve<R>(h, up, vp, false);
   if (rc != SBIM_OK) return rc;
   if (h->symmetric) correct_kernel<R, true><<<g, kThreads, 0, h->stream>>>(u, v, vp, np, dt);
   else correct_kernel<R, false><<<g, kThreads, 0, h->stream>>>(u, v, vp, np, dt);
   FCU(cudaGetLastError());
-  rc = solve<R>(h, u, v);
+  rc = solve<R>(h, u, v, true);
   if (rc != SBIM_OK) return rc;
   ++h->n;
   return SBIM_OK;

@@ -13,7 +13,15 @@ struct MeshArgs {
   int fault;          // 1 if the plane at layer f is split
   double area;        // h^2: nodal area of boundary and fault nodes
   double half_mass;   // rho h^3 / 2: mass from the 4 elements on one side of a node
-  const void* stencil;  // [2][18][3][3] blocks (float or double, as the fields)
+};
+
+// The assembled hex8 stiffness as a 27-point stencil of 3x3 blocks, split by the
+// element layer it comes from: [side: below, above][18 = (ox, oy, oz)][3][3].
+// Passed to the kernels by value, so its entries are kernel-parameter constants
+// that the multiply-adds read directly (no load instruction per entry).
+template <class R>
+struct Stencil {
+  R s[2 * 18 * 9];
 };
 
 template <class R>
@@ -42,14 +50,14 @@ struct AdjointArgs {
 // stage 0: recompute u_new, v_pred; 1: corrector transpose; 2: fault transpose;
 // 3: mass and SBIM cotangents; 4: stiffness transpose; 5: predictor transpose.
 template <class R>
-cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const FaultArgs<R>& fa,
-                           int stage, cudaStream_t st);
+cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const Stencil<R>& S,
+                           const FaultArgs<R>& fa, int stage, cudaStream_t st);
 template <class R> cudaError_t layer_add(R* dst, const R* src, long long n, cudaStream_t st);
 
 template <class R> cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st);
 template <class R>
-cudaError_t force(const R* u, R* an, const MeshArgs& g, const R* tau_top, const R* tau_bot,
-                  const R* src, cudaStream_t st);
+cudaError_t force(const R* u, R* an, const MeshArgs& g, const Stencil<R>& S, const R* tau_top,
+                  const R* tau_bot, const R* src, cudaStream_t st);
 template <class R>
 cudaError_t fault(const R* u, const R* vpred, const R* a, R* an, const MeshArgs& g,
                   const FaultArgs<R>& fa, R dt, int weld, cudaStream_t st);

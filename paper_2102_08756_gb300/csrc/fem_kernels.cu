@@ -35,21 +35,25 @@ __global__ void predict_kernel(R* __restrict__ u, R* __restrict__ v, const R* __
   }
 }
 
-// an = (-K u + f_boundary) / m: the acceleration without fault traction.
-// f_boundary = +A tau_top on the top layer, -A tau_bot on the bottom layer.
+// F -= K x at node (i1, i3, layer l): the blocks of the element layers below
+// (side 0, layers l-1 and l) and above (side 1, layers l and l+1) the node that
+// exist (none across the split fault plane or past the slab's faces).  Fully
+// unrolled: every stencil index is a compile-time constant.
 template <class R>
-__global__ void force_kernel(const R* __restrict__ u, R* __restrict__ an, MeshArgs g,
-                             const R* __restrict__ tau_top, const R* __restrict__ tau_bot,
-                             const R* __restrict__ src) {
-  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i3 = blockIdx.y;
-  const int l = blockIdx.z;
-  if (i1 >= g.n1) return;
+__device__ __forceinline__ void stencil_apply(const R* __restrict__ x, const MeshArgs& g,
+                                              const Stencil<R>& S, int i1, int i3, int l,
+                                              bool down, bool up, R (&F)[3]) {
   const long long plane = (long long)g.n1 * g.n3;
-  const R* __restrict__ S = reinterpret_cast<const R*>(g.stencil);
-  const bool down = l > 0 && !(g.fault && l == g.f + 1);
-  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
-  R F[3] = {(R)0, (R)0, (R)0};
+  int j3s[3], j1s[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    int j3 = i3 + o - 1;
+    j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
+    int j1 = i1 + o - 1;
+    j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
+    j3s[o] = j3;
+    j1s[o] = j1;
+  }
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     if (side == 0 ? !down : !up) continue;
@@ -57,26 +61,38 @@ __global__ void force_kernel(const R* __restrict__ u, R* __restrict__ an, MeshAr
 #pragma unroll
     for (int oy = 0; oy < 2; ++oy) {
       const int ly = l + (side == 0 ? oy - 1 : oy);
-      const R* ul = u + (long long)ly * 3 * plane;
+      const R* xl = x + (long long)ly * 3 * plane;
 #pragma unroll
       for (int oz = 0; oz < 3; ++oz) {
-        int j3 = i3 + oz - 1;
-        j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
 #pragma unroll
         for (int ox = 0; ox < 3; ++ox) {
-          int j1 = i1 + ox - 1;
-          j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
-          const long long q = (long long)j3 * g.n1 + j1;
-          const R u0 = __ldg(ul + q), u1 = __ldg(ul + plane + q), u2 = __ldg(ul + 2 * plane + q);
+          const long long q = (long long)j3s[oz] * g.n1 + j1s[ox];
+          const R x0 = __ldg(xl + q), x1 = __ldg(xl + plane + q), x2 = __ldg(xl + 2 * plane + q);
           const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            F[c] -= __ldg(S + s + 3 * c) * u0 + __ldg(S + s + 3 * c + 1) * u1 +
-                    __ldg(S + s + 3 * c + 2) * u2;
+            F[c] -= S.s[s + 3 * c] * x0 + S.s[s + 3 * c + 1] * x1 + S.s[s + 3 * c + 2] * x2;
         }
       }
     }
   }
+}
+
+// an = (-K u + f_boundary) / m: the acceleration without fault traction.
+// f_boundary = +A tau_top on the top layer, -A tau_bot on the bottom layer.
+template <class R>
+__global__ void force_kernel(const R* __restrict__ u, R* __restrict__ an, MeshArgs g,
+                             const __grid_constant__ Stencil<R> S, const R* __restrict__ tau_top,
+                             const R* __restrict__ tau_bot, const R* __restrict__ src) {
+  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i3 = blockIdx.y;
+  const int l = blockIdx.z;
+  if (i1 >= g.n1) return;
+  const long long plane = (long long)g.n1 * g.n3;
+  const bool down = l > 0 && !(g.fault && l == g.f + 1);
+  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+  R F[3] = {(R)0, (R)0, (R)0};
+  stencil_apply(u, g, S, i1, i3, l, down, up, F);
   const long long q0 = (long long)i3 * g.n1 + i1;
   if (l == g.L - 1 && tau_top)
 #pragma unroll
@@ -294,38 +310,19 @@ __global__ void adj_mass_kernel(const R* __restrict__ laf, R* __restrict__ lF, M
 
 // out += -K x (the stiffness is symmetric: this is the transpose of -K u)
 template <class R>
-__global__ void stiffness_add_kernel(const R* __restrict__ x, R* __restrict__ out, MeshArgs g) {
+__global__ void stiffness_add_kernel(const R* __restrict__ x, R* __restrict__ out, MeshArgs g,
+                                     const __grid_constant__ Stencil<R> S) {
   const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int i3 = blockIdx.y;
   const int l = blockIdx.z;
   if (i1 >= g.n1) return;
   const long long plane = (long long)g.n1 * g.n3;
-  const R* __restrict__ S = reinterpret_cast<const R*>(g.stencil);
   const bool down = l > 0 && !(g.fault && l == g.f + 1);
   const bool up = l < g.L - 1 && !(g.fault && l == g.f);
   R F[3] = {(R)0, (R)0, (R)0};
-  for (int side = 0; side < 2; ++side) {
-    if (side == 0 ? !down : !up) continue;
-    const int base = side * 18 * 9;
-    for (int oy = 0; oy < 2; ++oy) {
-      const int ly = l + (side == 0 ? oy - 1 : oy);
-      const R* xl = x + (long long)ly * 3 * plane;
-      for (int oz = 0; oz < 3; ++oz) {
-        int j3 = i3 + oz - 1;
-        j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
-        for (int ox = 0; ox < 3; ++ox) {
-          int j1 = i1 + ox - 1;
-          j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
-          const long long qq = (long long)j3 * g.n1 + j1;
-          const R x0 = xl[qq], x1 = xl[plane + qq], x2 = xl[2 * plane + qq];
-          const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
-          for (int c = 0; c < 3; ++c)
-            F[c] -= S[s + 3 * c] * x0 + S[s + 3 * c + 1] * x1 + S[s + 3 * c + 2] * x2;
-        }
-      }
-    }
-  }
+  stencil_apply(x, g, S, i1, i3, l, down, up, F);
   R* ol = out + (long long)l * 3 * plane + (long long)i3 * g.n1 + i1;
+#pragma unroll
   for (int c = 0; c < 3; ++c) ol[c * plane] += F[c];
 }
 
@@ -365,11 +362,11 @@ cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st) 
 }
 
 template <class R>
-cudaError_t force(const R* u, R* an, const MeshArgs& g, const R* tau_top, const R* tau_bot,
-                  const R* src, cudaStream_t st) {
+cudaError_t force(const R* u, R* an, const MeshArgs& g, const Stencil<R>& S, const R* tau_top,
+                  const R* tau_bot, const R* src, cudaStream_t st) {
   const int tx = g.n1 >= 128 ? 128 : 32;
   const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
-  force_kernel<R><<<grid, tx, 0, st>>>(u, an, g, tau_top, tau_bot, src);
+  force_kernel<R><<<grid, tx, 0, st>>>(u, an, g, S, tau_top, tau_bot, src);
   return cudaGetLastError();
 }
 
@@ -396,8 +393,8 @@ cudaError_t fault_fields(const R* u, const R* v, const MeshArgs& g, R* slip, R* 
 }
 
 template <class R>
-cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const FaultArgs<R>& fa,
-                           int stage, cudaStream_t st) {
+cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const Stencil<R>& S,
+                           const FaultArgs<R>& fa, int stage, cudaStream_t st) {
   const long long n = (long long)g.L * 3 * g.n1 * g.n3;
   const long long plane = (long long)g.n1 * g.n3;
   const R dt = j.dt;
@@ -421,7 +418,7 @@ cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const Fau
     case 4: {
       const int tx = g.n1 >= 128 ? 128 : 32;
       const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
-      stiffness_add_kernel<R><<<grid, tx, 0, st>>>(j.lF, j.lun, g);
+      stiffness_add_kernel<R><<<grid, tx, 0, st>>>(j.lF, j.lun, g, S);
       break;
     }
     case 5:
@@ -442,14 +439,16 @@ cudaError_t layer_add(R* dst, const R* src, long long n, cudaStream_t st) {
 
 #define SBIM_FEM_INST(R)                                                                     \
   template cudaError_t predict<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
-  template cudaError_t force<R>(const R*, R*, const MeshArgs&, const R*, const R*, const R*, \
+  template cudaError_t force<R>(const R*, R*, const MeshArgs&, const Stencil<R>&, const R*,  \
+                                const R*, const R*,                                          \
                                 cudaStream_t);                                               \
   template cudaError_t fault<R>(const R*, const R*, const R*, R*, const MeshArgs&,           \
                                 const FaultArgs<R>&, R, int, cudaStream_t);                  \
   template cudaError_t correct<R>(R*, R*, const R*, long long, R, cudaStream_t);             \
   template cudaError_t fault_fields<R>(const R*, const R*, const MeshArgs&, R*, R*, cudaStream_t); \
   template cudaError_t adjoint_stages<R>(const AdjointArgs<R>&, const MeshArgs&,                  \
-                                         const FaultArgs<R>&, int, cudaStream_t);                \
+                                         const Stencil<R>&, const FaultArgs<R>&, int,            \
+                                         cudaStream_t);                                          \
   template cudaError_t layer_add<R>(R*, const R*, long long, cudaStream_t);
 SBIM_FEM_INST(float)
 SBIM_FEM_INST(double)

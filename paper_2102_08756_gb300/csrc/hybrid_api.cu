@@ -32,7 +32,8 @@ struct sbim_hybrid_ctx {
   void* mu_s = nullptr;
   void* tau0 = nullptr;
   void* traction = nullptr;
-  void* stencil = nullptr;
+  sbim::fem::Stencil<float> stencil_f;
+  sbim::fem::Stencil<double> stencil_d;
   void* adj[8] = {};        // reverse sweep: un, vp, af, lun, lvp, lan, lao, lF
   void* adjp[4] = {};       // tb_top, tb_bot, ub, vb ([3][n3][n1])
   double mu_k = 0, Dc = 1, sigma0 = 0;
@@ -139,9 +140,11 @@ sbim::fem::MeshArgs mesh_args(const sbim_hybrid_ctx* c) {
   g.n1 = c->n1; g.n3 = c->n3; g.L = c->L; g.f = c->n2 / 2; g.fault = c->fault;
   g.area = c->h * c->h;
   g.half_mass = 0.5 * c->rho * c->h * c->h * c->h;
-  g.stencil = c->stencil;
   return g;
 }
+
+const sbim::fem::Stencil<float>& stencil_of(const sbim_hybrid_ctx* c, float) { return c->stencil_f; }
+const sbim::fem::Stencil<double>& stencil_of(const sbim_hybrid_ctx* c, double) { return c->stencil_d; }
 
 // Stage (1): FE predictor.
 template <class R>
@@ -171,7 +174,7 @@ int stage_finish(sbim_hybrid_ctx* c, const void* src) {
   R* a = (R*)c->a;
   R* an = (R*)c->an;
   const sbim::fem::MeshArgs g = mesh_args(c);
-  HCU(sbim::fem::force<R>(u, an, g, c->boundaries ? (const R*)c->tau_top : nullptr,
+  HCU(sbim::fem::force<R>(u, an, g, stencil_of(c, R()), c->boundaries ? (const R*)c->tau_top : nullptr,
                           c->boundaries ? (const R*)c->tau_bot : nullptr, (const R*)src, st));
   if (c->fault) {
     sbim::fem::FaultArgs<R> fa;
@@ -243,10 +246,11 @@ int adjoint_impl(sbim_hybrid_ctx* c, const void* u, const void* v, const void* a
   sbim::fem::FaultArgs<R> fa;
   fa.mu_s = (const R*)c->mu_s; fa.tau0 = (const R*)c->tau0;
   fa.mu_k = (R)c->mu_k; fa.Dc = (R)c->Dc; fa.sigma0 = (R)c->sigma0; fa.traction = nullptr;
-  HCU(sbim::fem::adjoint_stages<R>(j, g, fa, 0, st));
-  HCU(sbim::fem::force<R>(j.un, j.af, g, c->boundaries ? (const R*)tau_top : nullptr,
+  HCU(sbim::fem::adjoint_stages<R>(j, g, stencil_of(c, R()), fa, 0, st));
+  HCU(sbim::fem::force<R>(j.un, j.af, g, stencil_of(c, R()), c->boundaries ? (const R*)tau_top : nullptr,
                           c->boundaries ? (const R*)tau_bot : nullptr, nullptr, st));
-  for (int stage = 1; stage <= 4; ++stage) HCU(sbim::fem::adjoint_stages<R>(j, g, fa, stage, st));
+  for (int stage = 1; stage <= 4; ++stage)
+    HCU(sbim::fem::adjoint_stages<R>(j, g, stencil_of(c, R()), fa, stage, st));
   if (c->boundaries) {
     const long long lay = 3 * c->plane();
     R* ub = (R*)c->adjp[2];
@@ -260,7 +264,7 @@ int adjoint_impl(sbim_hybrid_ctx* c, const void* u, const void* v, const void* a
     HCU(sbim::fem::layer_add<R>(j.lun, ub, lay, st));
     HCU(sbim::fem::layer_add<R>(j.lvp, vb, lay, st));
   }
-  HCU(sbim::fem::adjoint_stages<R>(j, g, fa, 5, st));
+  HCU(sbim::fem::adjoint_stages<R>(j, g, stencil_of(c, R()), fa, 5, st));
   ++c->n;
   return SBIM_OK;
 }
@@ -270,7 +274,7 @@ void hrelease(sbim_hybrid_ctx* c) {
   sbim_destroy(c->top);
   sbim_destroy(c->bot);
   void* p[] = {c->u,     c->v,     c->a,        c->an,      c->tau_top,
-               c->tau_bot, c->mu_s, c->tau0, c->traction, c->stencil};
+               c->tau_bot, c->mu_s, c->tau0, c->traction};
   for (void* x : p)
     if (x) cudaFree(x);
   for (void* x : c->adj)
@@ -312,25 +316,17 @@ int sbim_hybrid_create(sbim_hybrid* out, int n1, int n2, int n3, double h, doubl
   alloc(&c->u, fb); alloc(&c->v, fb); alloc(&c->a, fb); alloc(&c->an, fb);
   alloc(&c->tau_top, pb); alloc(&c->tau_bot, pb); alloc(&c->traction, pb);
   alloc(&c->mu_s, c->plane() * c->rs); alloc(&c->tau0, c->plane() * c->rs);
-  alloc(&c->stencil, 324 * c->rs);
   if (rc == SBIM_OK && c->boundaries) {
     rc = sbim_create(&c->top, n1, n3, n1 * h, n3 * h, cs, cp, rho, dt, n_cut, +1, precision, 1, stream);
     if (rc == SBIM_OK)
       rc = sbim_create(&c->bot, n1, n3, n1 * h, n3 * h, cs, cp, rho, dt, n_cut, -1, precision, 1, stream);
   }
   if (rc == SBIM_OK) {
-    double K[24][24], S[324];
+    double K[24][24];
     const double mu = rho * cs * cs, lam = rho * cp * cp - 2 * mu;
     hex8_stiffness(h, lam, mu, K);
-    build_stencil(K, S);
-    float Sf[324];
-    for (int i = 0; i < 324; ++i) Sf[i] = (float)S[i];
-    const void* src = precision == SBIM_FP64 ? (const void*)S : (const void*)Sf;
-    const cudaError_t e = cudaMemcpyAsync(c->stencil, src, 324 * c->rs, cudaMemcpyHostToDevice,
-                                          c->stream);
-    if (e != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "stencil upload: %s", cudaGetErrorString(e));
-    if (rc == SBIM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
-      rc = hfail(SBIM_ERR_CUDA, "sync");
+    build_stencil(K, c->stencil_d.s);
+    for (int i = 0; i < 324; ++i) c->stencil_f.s[i] = (float)c->stencil_d.s[i];
   }
   if (rc == SBIM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "sync");
   if (rc != SBIM_OK) {

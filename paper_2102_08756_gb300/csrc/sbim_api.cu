@@ -139,6 +139,7 @@ struct sbim_ctx {
   bool have_fwd = false, have_inv = false;
 
   long long n = 0;
+  bool can_repeat = false;    // the partial sums hold the last forward level
   double tau_inf[3] = {0, 0, 0};
 
   bool prof = false;
@@ -489,7 +490,10 @@ int handle_epilogue(sbim_handle c, const void* v, void* tau) {
   return SBIM_OK;
 }
 
-void handle_advance(sbim_handle c) { ++c->n; }
+void handle_advance(sbim_handle c) {
+  ++c->n;
+  c->can_repeat = false;   // the batch kept its partial sums in its own buffers
+}
 
 int handle_shape(sbim_handle c, int* precision, int* kahan, int* variant, void** stream) {
   *precision = c->prec;
@@ -546,8 +550,13 @@ namespace {
 // matrix is Hermitian in the (xi, 2, perp) frame ([a, ib; -ib, d] and a real
 // perp entry), so the transpose of R2C -> A -> C2R/N is the same map; applied to
 // the tau_bar sequence in reverse time it gives the time-reversed correlation.
-int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoint) {
+int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoint,
+             bool repeat = false) {
   cudaStream_t st = c->stream;
+  if (repeat) {                     // back to the level being re-evaluated
+    CU(sbim::launch_rewind(c->d_step, st));
+    --c->n;
+  }
   cudaEvent_t* e = nullptr;
   if (c->prof) {
     if (c->prof_issued - c->prof_harvested >= kProfRing) {
@@ -563,7 +572,9 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
     CF(cufftExecR2C(c->plan_fwd, (cufftReal*)in, (cufftComplex*)c->d_uhat));
   if (e) CU(cudaEventRecord(e[1], st));
   const sbim::StepArgs a = step_args(c);
-  if (c->variant >= 1)
+  if (repeat)
+    CU(sbim::launch_repeat_lag0(a, c->prec, st));
+  else if (c->variant >= 1)
     CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st));
   else
     CU(sbim::launch_conv(a, c->prec, c->kahan, st));
@@ -589,6 +600,7 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
     ++c->prof_issued;
   }
   ++c->n;
+  c->can_repeat = !adjoint;
   return SBIM_OK;
 }
 
@@ -600,6 +612,15 @@ int sbim_step(sbim_handle h, const void* u, const void* v, void* tau) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
   if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
   return run_step(h, u, v, tau, false);
+}
+
+int sbim_step_repeat(sbim_handle h, const void* u, const void* v, void* tau) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
+  if (!h->can_repeat || h->n == 0)
+    return fail(SBIM_ERR_STATE, "sbim_step_repeat needs a preceding sbim_step on this handle "
+                                "(with no other call that changes its state in between)");
+  return run_step(h, u, v, tau, false, true);
 }
 
 int sbim_step_adjoint(sbim_handle h, const void* tau_bar, void* u_bar, void* v_bar) {
@@ -631,6 +652,7 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
 int sbim_set_window(sbim_handle h, double window) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
   if (!(window >= 0)) return fail(SBIM_ERR_ARG, "window must be >= 0");
+  h->can_repeat = false;
   if (window == 0) {
     h->window = 0;
     return SBIM_OK;
@@ -671,6 +693,7 @@ int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
   if (variant < 0 || variant > 3) return fail(SBIM_ERR_ARG, "variant must be 0..3");
   if (lags_per_cta < 0) return fail(SBIM_ERR_ARG, "lags_per_cta must be >= 0");
+  h->can_repeat = false;
   const int old_v = h->variant, old_l = h->lags_per_cta, old_lc = h->lc, old_nc = h->nchunks;
   h->variant = variant;
   h->lags_per_cta = lags_per_cta;
@@ -701,6 +724,7 @@ int sbim_reset(sbim_handle h) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
   CU(cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream));
   h->n = 0;
+  h->can_repeat = false;
   return SBIM_OK;
 }
 
@@ -709,6 +733,7 @@ int sbim_rewind(sbim_handle h) {
   if (h->n == 0) return fail(SBIM_ERR_STATE, "no step to rewind");
   CU(sbim::launch_rewind(h->d_step, h->stream));
   --h->n;
+  h->can_repeat = false;
   return SBIM_OK;
 }
 
@@ -786,6 +811,7 @@ int sbim_load(sbim_handle h, const void* buf, size_t bytes) {
   CU(cudaMemcpyAsync(h->d_step, &hd.n, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->n = hd.n;
+  h->can_repeat = false;
   for (int i = 0; i < 3; ++i) h->tau_inf[i] = hd.tau_inf[i];
   return SBIM_OK;
 }

@@ -124,29 +124,43 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   C D[3][4];
   rotate_current(a, o, D);
 
+  // Chunk reduction of the 4 x kFields sums: the chunk loop is outermost so that
+  // each iteration issues 40 independent loads (each sum's own order over the
+  // chunks, and its compensation, are those of a per-sum loop).
+  R sum[4][kFields], cmp[4][kFields];
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int k = 0; k < kFields; ++k) { sum[g][k] = (R)0; cmp[g][k] = (R)0; }
+  for (int ch = 0; ch < nch; ++ch) {
+    R x[4][kFields];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int k = 0; k < kFields; ++k)
+        x[g][k] = part[((long long)ch * (4 * kFields) + g * kFields + k) * orb + o];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int k = 0; k < kFields; ++k) {
+        if (KAHAN) {
+          const R y = x[g][k] - cmp[g][k];
+          const R t = sum[g][k] + y;
+          cmp[g][k] = (t - sum[g][k]) - y;
+          sum[g][k] = t;
+        } else {
+          sum[g][k] += x[g][k];
+        }
+      }
+  }
+
   int pend = -1;
   C P1, P2, P3;
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     const int b = a.bin[o * 4 + g];
     if (b < 0) continue;
-    R v[kFields];
-#pragma unroll
-    for (int k = 0; k < kFields; ++k) {
-      R s = (R)0, c = (R)0;
-      for (int ch = 0; ch < nch; ++ch) {
-        const R x = part[((long long)ch * (4 * kFields) + g * kFields + k) * orb + o];
-        if (KAHAN) {
-          const R y = x - c;
-          const R t = s + y;
-          c = (t - s) - y;
-          s = t;
-        } else {
-          s += x;
-        }
-      }
-      v[k] = s;
-    }
+    const R* v = sum[g];
     const C dxi = D[0][g], d2 = D[1][g];
     // F_xi = -side mu q C11 + i mu q [(2 - eta) D_2 + C12a]
     const R bxr = inst * d2.x + v[6], bxi = inst * d2.y + v[7];
@@ -226,6 +240,47 @@ __global__ void adjoint_epilogue_kernel(const R* __restrict__ tau_bar, R* __rest
     v_bar[i] = -coef * tau_bar[i];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
+}
+
+// Re-evaluation of the current level with a new displacement (sbim_step_repeat).
+// Every lag >= 1 of the truncated convolution is unchanged, so chunk 0's partial
+// sums take w(0) (D_new - D_old) and the ring slot takes D_new; the assembly then
+// runs as usual.  Lag 0 is in chunk 0 of every orbit (its lag limit is >= 1).
+template <class S>
+__global__ void __launch_bounds__(kOrbitTile) repeat_lag0_kernel(const StepArgs a) {
+  using R = typename S::real;
+  using C = typename S::cplx;
+  using T4 = typename S::tab4;
+  const int o = blockIdx.x * kOrbitTile + threadIdx.x;
+  if (o >= a.n_orb_pad) return;
+  const long long n = *a.step;
+  const int sn = (int)(n % a.n_cut);
+  const long long orb = a.n_orb_pad;
+  C Dn[3][4], Do[3][4];
+  rotate_current(a, o, Dn);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long rec = ((long long)sn * 3 + c) * orb + o;
+    S::load(a.hist, rec, a.slot_stride, Do[c]);
+    S::store(a.hist, rec, a.slot_stride, Dn[c]);
+    S::round(Dn[c]);
+  }
+  R w[4];
+  lag_weights(reinterpret_cast<const T4*>(a.table), 0ull,
+              reinterpret_cast<const R*>(a.dT)[o] * (R)0.5, w);
+  R* part = reinterpret_cast<R*>(a.part);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    C x, d2, dp;
+    x.x = Dn[0][g].x - Do[0][g].x;  x.y = Dn[0][g].y - Do[0][g].y;
+    d2.x = Dn[1][g].x - Do[1][g].x; d2.y = Dn[1][g].y - Do[1][g].y;
+    dp.x = Dn[2][g].x - Do[2][g].x; dp.y = Dn[2][g].y - Do[2][g].y;
+    // the field order of accumulate(): C11 (xi), C33 (perp), C22 (2), C12a (2), C12b (xi)
+    const R add[kFields] = {w[0] * x.x,  w[0] * x.y,  w[2] * dp.x, w[2] * dp.y, w[1] * d2.x,
+                            w[1] * d2.y, w[3] * d2.x, w[3] * d2.y, w[3] * x.x,  w[3] * x.y};
+#pragma unroll
+    for (int k = 0; k < kFields; ++k) part[((long long)g * kFields + k) * orb + o] += add[k];
+  }
 }
 
 // Step counter one back (sbim_rewind): the next step rewrites the same ring slot.
@@ -317,6 +372,18 @@ cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, v
         (const float*)s_field, (const float*)v, (float*)tau, plane, (float)coef[0],
         (float)coef[1], (float)coef[2], (float)tau_inf[0], (float)tau_inf[1],
         (float)tau_inf[2], step);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st) {
+  const unsigned grid = (unsigned)(a.n_orb_pad / kOrbitTile);
+  switch (precision) {
+    case SBIM_FP64: repeat_lag0_kernel<StoreF64><<<grid, kOrbitTile, 0, st>>>(a); break;
+    case SBIM_FP32: repeat_lag0_kernel<StoreF32><<<grid, kOrbitTile, 0, st>>>(a); break;
+    case SBIM_BF16X2: repeat_lag0_kernel<StoreBF16<true>><<<grid, kOrbitTile, 0, st>>>(a); break;
+    case SBIM_BF16: repeat_lag0_kernel<StoreBF16<false>><<<grid, kOrbitTile, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

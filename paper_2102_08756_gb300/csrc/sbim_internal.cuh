@@ -81,6 +81,7 @@ int conv_tma_ctas_per_sm(int precision, int shape);
 cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_rewind(long long* step, cudaStream_t st);
+cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st);
 cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
                             long long plane, const double coef[3], const double tau_inf[3],
                             long long* step, cudaStream_t st);

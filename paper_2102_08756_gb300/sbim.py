@@ -44,6 +44,7 @@ def lib():
     L.sbim_set_far_field.argtypes = [vp, ctypes.POINTER(d)]
     L.sbim_reset.argtypes = [vp]
     L.sbim_rewind.argtypes = [vp]
+    L.sbim_step_repeat.argtypes = [vp, vp, vp, vp]
     L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
     L.sbim_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -137,6 +138,10 @@ def sbim_set_far_field(h, tau_inf):
 
 def sbim_reset(h):
     _check(lib().sbim_reset(h))
+
+
+def sbim_step_repeat(h, u_ptr, v_ptr, tau_ptr):
+    _check(lib().sbim_step_repeat(h, u_ptr, v_ptr, tau_ptr))
 
 
 def sbim_rewind(h):
@@ -402,6 +407,13 @@ class SBIM:
         if tau is None:
             tau = self.torch.empty_like(u)
         sbim_step(self.h, self._field(u, "u"), self._field(v, "v"), self._field(tau, "tau"))
+        return tau
+
+    def step_repeat(self, u, v, tau=None):
+        """The last step's level again with a new u, v (see include/sbim.h)."""
+        if tau is None:
+            tau = self.torch.empty_like(u)
+        sbim_step_repeat(self.h, self._field(u, "u"), self._field(v, "v"), self._field(tau, "tau"))
         return tau
 
     def step_adjoint(self, tau_bar, u_bar=None, v_bar=None):

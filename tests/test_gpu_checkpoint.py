@@ -104,3 +104,47 @@ def test_rewind_reevaluates_the_level(precision):
     assert a.n == 8
     assert torch.equal(a.step(x[0], x[1]), b.step(x[0], x[1]))
     assert torch.equal(a.step(x[2], x[3]), b.step(x[2], x[3]))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16x2", "bf16"])
+@pytest.mark.parametrize("variant,window", [(None, 0.0), (0, 0.0), (None, 3.0)])
+def test_step_repeat_equals_rewind_and_step(precision, variant, window):
+    """sbim_step_repeat re-evaluates the last level with a new displacement: the
+    result matches sbim_rewind + sbim_step to rounding, and the ring slot it
+    writes is the same, so every later step is bit-identical."""
+    from paper_2102_08756_gb300.sbim import SBIMError
+    n1, n3, n_cut = 20, 12, 7
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    g = torch.Generator().manual_seed(4)
+    x = [torch.randn((3, n3, n1), generator=g, dtype=torch.float64).to("cuda", tdt) * 1e-3
+         for _ in range(16)]
+    a = _make(n1, n3, n_cut, precision)
+    b = _make(n1, n3, n_cut, precision)
+    for h in (a, b):
+        if variant is not None:
+            h.set_conv_config(variant)
+        if window:
+            h.set_window(window)
+    with pytest.raises(SBIMError):
+        a.step_repeat(x[0], x[1])
+    for m in range(9):                               # past the cutoff
+        a.step(x[m], x[m + 1])
+        b.step(x[m], x[m + 1])
+    a.step(x[9], x[10])
+    b.step(x[9], x[10])
+    ra = a.step_repeat(x[11], x[12])
+    ra2 = a.step_repeat(x[13], x[14])                # a repeat can be repeated
+    b.rewind()
+    b.step(x[11], x[12])
+    b.rewind()
+    rb2 = b.step(x[13], x[14])
+    assert a.n == b.n == 10
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    scale = float(rb2.abs().max())
+    assert float((ra2 - rb2).abs().max()) < tol * scale
+    assert float((ra - ra2).abs().max()) > 0          # the new displacement mattered
+    for m in range(3):
+        assert torch.equal(a.step(x[m], x[m + 4]), b.step(x[m], x[m + 4]))
+    a.rewind()
+    with pytest.raises(SBIMError):
+        a.step_repeat(x[0], x[1])
