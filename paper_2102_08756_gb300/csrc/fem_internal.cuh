@@ -15,8 +15,9 @@ struct MeshArgs {
   double half_mass;   // rho h^3 / 2: mass from the 4 elements on one side of a node
 };
 
-// The assembled hex8 stiffness as a 27-point stencil of 3x3 blocks, split by the
-// element layer it comes from: [side: below, above][18 = (ox, oy, oz)][3][3].
+// The assembled hex8 stiffness, negated (-K), as a 27-point stencil of 3x3
+// blocks split by the element layer it comes from: [side: below, above]
+// [18 = (ox, oy, oz)][3][3].
 // Passed to the kernels by value, so its entries are kernel-parameter constants
 // that the multiply-adds read directly (no load instruction per entry).
 template <class R>

@@ -35,10 +35,11 @@ __global__ void predict_kernel(R* __restrict__ u, R* __restrict__ v, const R* __
   }
 }
 
-// F -= K x at node (i1, i3, layer l): the blocks of the element layers below
+// F += (-K) x at node (i1, i3, layer l): the blocks of the element layers below
 // (side 0, layers l-1 and l) and above (side 1, layers l and l+1) the node that
 // exist (none across the split fault plane or past the slab's faces).  Fully
-// unrolled: every stencil index is a compile-time constant.
+// unrolled: every stencil index is a compile-time constant, and the stencil
+// holds -K so that each entry is one fused multiply-add.
 template <class R>
 __device__ __forceinline__ void stencil_apply(const R* __restrict__ x, const MeshArgs& g,
                                               const Stencil<R>& S, int i1, int i3, int l,
@@ -70,8 +71,11 @@ __device__ __forceinline__ void stencil_apply(const R* __restrict__ x, const Mes
           const R x0 = __ldg(xl + q), x1 = __ldg(xl + plane + q), x2 = __ldg(xl + 2 * plane + q);
           const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            F[c] -= S.s[s + 3 * c] * x0 + S.s[s + 3 * c + 1] * x1 + S.s[s + 3 * c + 2] * x2;
+          for (int c = 0; c < 3; ++c) {
+            F[c] = fma(S.s[s + 3 * c], x0, F[c]);
+            F[c] = fma(S.s[s + 3 * c + 1], x1, F[c]);
+            F[c] = fma(S.s[s + 3 * c + 2], x2, F[c]);
+          }
         }
       }
     }

@@ -326,7 +326,10 @@ int sbim_hybrid_create(sbim_hybrid* out, int n1, int n2, int n3, double h, doubl
     const double mu = rho * cs * cs, lam = rho * cp * cp - 2 * mu;
     hex8_stiffness(h, lam, mu, K);
     build_stencil(K, c->stencil_d.s);
-    for (int i = 0; i < 324; ++i) c->stencil_f.s[i] = (float)c->stencil_d.s[i];
+    for (int i = 0; i < 324; ++i) {
+      c->stencil_d.s[i] = -c->stencil_d.s[i];           // the kernels accumulate (-K) u
+      c->stencil_f.s[i] = (float)c->stencil_d.s[i];
+    }
   }
   if (rc == SBIM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = hfail(SBIM_ERR_CUDA, "sync");
   if (rc != SBIM_OK) {
