@@ -35,82 +35,122 @@ __global__ void predict_kernel(R* __restrict__ u, R* __restrict__ v, const R* __
   }
 }
 
-// F += (-K) x at node (i1, i3, layer l): the blocks of the element layers below
-// (side 0, layers l-1 and l) and above (side 1, layers l and l+1) the node that
-// exist (none across the split fault plane or past the slab's faces).  Fully
-// unrolled: every stencil index is a compile-time constant, and the stencil
-// holds -K so that each entry is one fused multiply-add.
+// One node layer of a field around a node: [component][oz][ox], the 3 x 3
+// in-plane neighbourhood (periodic in x1 and x3).
 template <class R>
-__device__ __forceinline__ void stencil_apply(const R* __restrict__ x, const MeshArgs& g,
-                                              const Stencil<R>& S, int i1, int i3, int l,
-                                              bool down, bool up, R (&F)[3]) {
-  const long long plane = (long long)g.n1 * g.n3;
-  int j3s[3], j1s[3];
+struct Window {
+  R v[3][3][3];
+};
+
+template <class R>
+__device__ __forceinline__ void load_window(const R* __restrict__ xl, long long plane,
+                                            const long long (&q)[3][3], Window<R>& w) {
 #pragma unroll
-  for (int o = 0; o < 3; ++o) {
-    int j3 = i3 + o - 1;
-    j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
-    int j1 = i1 + o - 1;
-    j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
-    j3s[o] = j3;
-    j1s[o] = j1;
-  }
+  for (int c = 0; c < 3; ++c)
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (side == 0 ? !down : !up) continue;
-    const int base = side * 18 * 9;
+    for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
-    for (int oy = 0; oy < 2; ++oy) {
-      const int ly = l + (side == 0 ? oy - 1 : oy);
-      const R* xl = x + (long long)ly * 3 * plane;
+      for (int ox = 0; ox < 3; ++ox) w.v[c][oz][ox] = __ldg(xl + c * plane + q[oz][ox]);
+}
+
+// F += (-K) x from the element layer on one side of the node: side 0 (below)
+// spans node layers l-1 (lo) and l (hi), side 1 (above) layers l and l+1.  Fully
+// unrolled: every stencil index is a compile-time constant, and the stencil holds
+// -K so that each entry is one fused multiply-add.
+template <int SIDE, class R>
+__device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>& lo,
+                                           const Window<R>& hi, R (&F)[3]) {
 #pragma unroll
-      for (int oz = 0; oz < 3; ++oz) {
+  for (int oy = 0; oy < 2; ++oy) {
+    const Window<R>& w = oy == 0 ? lo : hi;
 #pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-          const long long q = (long long)j3s[oz] * g.n1 + j1s[ox];
-          const R x0 = __ldg(xl + q), x1 = __ldg(xl + plane + q), x2 = __ldg(xl + 2 * plane + q);
-          const int s = base + ((ox * 2 + oy) * 3 + oz) * 9;
+    for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            F[c] = fma(S.s[s + 3 * c], x0, F[c]);
-            F[c] = fma(S.s[s + 3 * c + 1], x1, F[c]);
-            F[c] = fma(S.s[s + 3 * c + 2], x2, F[c]);
-          }
+      for (int ox = 0; ox < 3; ++ox) {
+        const int s = SIDE * 18 * 9 + ((ox * 2 + oy) * 3 + oz) * 9;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F[c] = fma(S.s[s + 3 * c], w.v[0][oz][ox], F[c]);
+          F[c] = fma(S.s[s + 3 * c + 1], w.v[1][oz][ox], F[c]);
+          F[c] = fma(S.s[s + 3 * c + 2], w.v[2][oz][ox], F[c]);
         }
       }
+  }
+}
+
+// The stencil -K x for every node of one (i1, i3) column, marching up the node
+// layers with two register windows: at layer l one holds layer l-1 and the other
+// layer l; after the blocks below the node are applied, the first is reloaded
+// with layer l+1 for the blocks above, and the two swap roles for layer l+1.
+// Each layer of x is loaded once per column (27 values), not once per
+// neighbouring node layer.  A layer's element blocks below (down) and above (up)
+// exist unless they cross the split fault plane or the slab's faces.  Per node,
+// epi(l, q0, down, up, F) finishes.
+template <class R, class Epi>
+__device__ __forceinline__ void stencil_column(const R* __restrict__ x, const MeshArgs& g,
+                                               const Stencil<R>& S, int i1, int i3, Epi epi) {
+  const long long plane = (long long)g.n1 * g.n3;
+  long long q[3][3];
+#pragma unroll
+  for (int oz = 0; oz < 3; ++oz) {
+    int j3 = i3 + oz - 1;
+    j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
+#pragma unroll
+    for (int ox = 0; ox < 3; ++ox) {
+      int j1 = i1 + ox - 1;
+      j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
+      q[oz][ox] = (long long)j3 * g.n1 + j1;
     }
+  }
+  const long long q0 = (long long)i3 * g.n1 + i1;
+  const long long layer = 3 * plane;
+  int l = 0;
+  auto node = [&](Window<R>& prev, Window<R>& cur) {
+    const bool down = l > 0 && !(g.fault && l == g.f + 1);
+    const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+    R F[3] = {(R)0, (R)0, (R)0};
+    if (down) apply_side<0>(S, prev, cur, F);
+    if (l + 1 < g.L) load_window(x + (l + 1) * layer, plane, q, prev);   // prev := layer l+1
+    if (up) apply_side<1>(S, cur, prev, F);
+    epi(l, q0, down, up, F);
+    ++l;
+  };
+  Window<R> A, B;
+  load_window(x, plane, q, B);
+  while (l < g.L) {
+    node(A, B);
+    if (l >= g.L) break;
+    node(B, A);
   }
 }
 
 // an = (-K u + f_boundary) / m: the acceleration without fault traction.
 // f_boundary = +A tau_top on the top layer, -A tau_bot on the bottom layer.
 template <class R>
-__global__ void force_kernel(const R* __restrict__ u, R* __restrict__ an, MeshArgs g,
-                             const __grid_constant__ Stencil<R> S, const R* __restrict__ tau_top,
-                             const R* __restrict__ tau_bot, const R* __restrict__ src) {
+__global__ void __launch_bounds__(128) force_kernel(const R* __restrict__ u, R* __restrict__ an,
+                                                    MeshArgs g, const __grid_constant__ Stencil<R> S,
+                                                    const R* __restrict__ tau_top,
+                                                    const R* __restrict__ tau_bot,
+                                                    const R* __restrict__ src) {
   const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int i3 = blockIdx.y;
-  const int l = blockIdx.z;
   if (i1 >= g.n1) return;
   const long long plane = (long long)g.n1 * g.n3;
-  const bool down = l > 0 && !(g.fault && l == g.f + 1);
-  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
-  R F[3] = {(R)0, (R)0, (R)0};
-  stencil_apply(u, g, S, i1, i3, l, down, up, F);
-  const long long q0 = (long long)i3 * g.n1 + i1;
-  if (l == g.L - 1 && tau_top)
+  stencil_column(u, g, S, i1, i3, [&](int l, long long q0, bool down, bool up, R(&F)[3]) {
+    if (l == g.L - 1 && tau_top)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F[c] += g.area * tau_top[c * plane + q0];
-  if (l == 0 && tau_bot)
+      for (int c = 0; c < 3; ++c) F[c] += g.area * tau_top[c * plane + q0];
+    if (l == 0 && tau_bot)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F[c] -= g.area * tau_bot[c * plane + q0];
-  const R inv_m = (R)1 / ((down ? (R)g.half_mass : (R)0) + (up ? (R)g.half_mass : (R)0));
-  R* al = an + (long long)l * 3 * plane;
+      for (int c = 0; c < 3; ++c) F[c] -= g.area * tau_bot[c * plane + q0];
+    const R inv_m = (R)1 / ((down ? (R)g.half_mass : (R)0) + (up ? (R)g.half_mass : (R)0));
+    R* al = an + (long long)l * 3 * plane;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R extra = src ? src[((long long)l * 3 + c) * plane + q0] : (R)0;
-    al[c * plane + q0] = (F[c] + extra) * inv_m;
-  }
+    for (int c = 0; c < 3; ++c) {
+      const R extra = src ? src[((long long)l * 3 + c) * plane + q0] : (R)0;
+      al[c * plane + q0] = (F[c] + extra) * inv_m;
+    }
+  });
 }
 
 // Fault traction by the forward Lagrange-multiplier method (Eqs. (freeslip),
@@ -314,20 +354,18 @@ __global__ void adj_mass_kernel(const R* __restrict__ laf, R* __restrict__ lF, M
 
 // out += -K x (the stiffness is symmetric: this is the transpose of -K u)
 template <class R>
-__global__ void stiffness_add_kernel(const R* __restrict__ x, R* __restrict__ out, MeshArgs g,
-                                     const __grid_constant__ Stencil<R> S) {
+__global__ void __launch_bounds__(128) stiffness_add_kernel(const R* __restrict__ x,
+                                                            R* __restrict__ out, MeshArgs g,
+                                                            const __grid_constant__ Stencil<R> S) {
   const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int i3 = blockIdx.y;
-  const int l = blockIdx.z;
   if (i1 >= g.n1) return;
   const long long plane = (long long)g.n1 * g.n3;
-  const bool down = l > 0 && !(g.fault && l == g.f + 1);
-  const bool up = l < g.L - 1 && !(g.fault && l == g.f);
-  R F[3] = {(R)0, (R)0, (R)0};
-  stencil_apply(x, g, S, i1, i3, l, down, up, F);
-  R* ol = out + (long long)l * 3 * plane + (long long)i3 * g.n1 + i1;
+  stencil_column(x, g, S, i1, i3, [&](int l, long long q0, bool, bool, R(&F)[3]) {
+    R* ol = out + (long long)l * 3 * plane + q0;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) ol[c * plane] += F[c];
+    for (int c = 0; c < 3; ++c) ol[c * plane] += F[c];
+  });
 }
 
 // dst[layer][...] += src[...] on one layer (boundary cotangents from the SBIM transposes)
@@ -369,7 +407,7 @@ template <class R>
 cudaError_t force(const R* u, R* an, const MeshArgs& g, const Stencil<R>& S, const R* tau_top,
                   const R* tau_bot, const R* src, cudaStream_t st) {
   const int tx = g.n1 >= 128 ? 128 : 32;
-  const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
+  const dim3 grid((g.n1 + tx - 1) / tx, g.n3);
   force_kernel<R><<<grid, tx, 0, st>>>(u, an, g, S, tau_top, tau_bot, src);
   return cudaGetLastError();
 }
@@ -421,7 +459,7 @@ cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const Ste
       break;
     case 4: {
       const int tx = g.n1 >= 128 ? 128 : 32;
-      const dim3 grid((g.n1 + tx - 1) / tx, g.n3, g.L);
+      const dim3 grid((g.n1 + tx - 1) / tx, g.n3);
       stiffness_add_kernel<R><<<grid, tx, 0, st>>>(j.lF, j.lun, g, S);
       break;
     }
