@@ -26,7 +26,12 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# The FP64 oracle baseline is timed on one host thread (its "cores" field): pin
+# the BLAS / OpenMP pools before numpy starts them.
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
