@@ -278,3 +278,29 @@ def test_truncation_window_matches_oracle(variant, grid, window):
             worst = max(worst, rel_l2(s, r))
     g.check()
     assert worst < 1e-5, worst
+
+
+@pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1)])
+@pytest.mark.parametrize("grid", [(2, 2, 200.0, 200.0), (2, 6, 200.0, 600.0), (6, 2, 600.0, 200.0)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_degenerate_grids(precision, kahan, grid, variant):
+    """The smallest grids: with n1 or n3 = 2 every mode along that axis is k = 0
+    or on its Nyquist line (a single orbit tile, mostly padding members)."""
+    n1, n3, L1, L3 = grid
+    es, et = run_parity(n1, n3, L1, L3, 5, 1, 14, precision, kahan, seed=n1 * 10 + n3,
+                        spectrum="k2", variant=variant)
+    assert es < TOL[precision] and et < TOL[precision], (es, et)
+
+
+def test_out_of_memory_is_reported_and_recoverable():
+    """A history that cannot fit (about 3 TB) fails with SBIM_ERR_OOM and
+    leaves the device usable: a normal handle is created and stepped after it."""
+    from paper_2102_08756_gb300.sbim import SBIM, SBIMError
+    with pytest.raises(SBIMError) as e:
+        SBIM(2048, 2048, 204800.0, 204800.0, CS, CP, RHO, 0.005, 65536, 1, "fp32", 1)
+    assert e.value.code == -2
+    h = SBIM(16, 16, 1600.0, 1600.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)
+    z = torch.zeros((3, 16, 16), device="cuda")
+    t = h.step(z, z)
+    torch.cuda.synchronize()
+    assert float(t.abs().max()) == 0.0
