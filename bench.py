@@ -46,6 +46,30 @@ BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 NCU_TRAFFIC = {"conv_src_sha1": "f48c0cd7a90671a809a89162abd5b5e973127271", "bytes_per_launch": 52.16e9 + 183.99e6}
 
 
+# The TPV3 benchmark as Section 3 states it (material, friction, prestress,
+# nucleation patch, rupture area, strip width and grid spacing), and the two
+# choices it leaves open (the nucleation overstress and the strength outside the
+# rupture area).
+TPV3 = dict(cs=3464.0, cp=6000.0, rho=2670.0, mu_s=0.677, mu_k=0.525, Dc=0.4, tau0=70e6,
+            sigma0=120e6, nucleation_size=3000.0, rupture_L1=30000.0, rupture_L3=15000.0,
+            strip_cells=4, dx=50.0)
+TPV3_OVERSTRESS = 1.005       # nucleation shear stress / (mu_s sigma0)
+TPV3_UNBREAKABLE_MU_S = 1e4   # static friction outside the rupture area
+
+
+def tpv3_law(X1, X3, Dc=None, prestress_ratio=None):
+    """(mu_s map, tau0 map, mu_k, Dc, sigma0) of TPV3 on node coordinates X1, X3
+    (m, centred on the fault); prestress_ratio replaces tau0 by
+    ratio * mu_s * sigma0 (ensemble scenarios)."""
+    T = TPV3
+    inside = (np.abs(X1) <= T["rupture_L1"] / 2) & (np.abs(X3) <= T["rupture_L3"] / 2)
+    patch = (np.abs(X1) <= T["nucleation_size"] / 2) & (np.abs(X3) <= T["nucleation_size"] / 2)
+    base = T["tau0"] if prestress_ratio is None else prestress_ratio * T["mu_s"] * T["sigma0"]
+    mu_s = np.where(inside, T["mu_s"], TPV3_UNBREAKABLE_MU_S)
+    tau0 = np.where(patch, TPV3_OVERSTRESS * T["mu_s"] * T["sigma0"], base)
+    return mu_s, tau0, T["mu_k"], T["Dc"] if Dc is None else Dc, T["sigma0"]
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -455,18 +479,15 @@ def run_coupled(args):
     _build.build()
     from paper_2102_08756_gb300.hybrid import Hybrid
     n1 = n3 = args.n or 512
-    n2, h, cs, cp, rho = 16, 100.0, 3464.0, 6000.0, 2670.0
+    n2, h = 16, 100.0
+    cs, cp, rho = TPV3["cs"], TPV3["cp"], TPV3["rho"]
     n_cut = args.n_cut or 2000
     dt = 0.3 * h / cp
     g = Hybrid(n1, n2, n3, h, cs, cp, rho, dt, n_cut, "fp32", True, True)
     x1 = (np.arange(n1) - n1 / 2 + 0.5) * h
     x3 = (np.arange(n3) - n3 / 2 + 0.5) * h
     X3, X1 = np.meshgrid(x3, x1, indexing="ij")
-    breakable = (np.abs(X1) <= 15e3) & (np.abs(X3) <= 7.5e3)
-    patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
-    mu_s = np.where(breakable, 0.677, 1e4)
-    tau0 = np.where(patch, 1.005 * 0.677 * 120e6, 70e6)
-    g.set_fault(mu_s, tau0, 0.525, 0.4, 120e6)
+    g.set_fault(*tpv3_law(X1, X3))
     K, W = args.steps, args.warmup
     for _ in range(n_cut + W):
         g.step()
@@ -519,17 +540,15 @@ def run_tpv3(args):
     _build.build()
     from paper_2102_08756_gb300.fault import FaultSolver
     from paper_2102_08756_gb300.hybrid import Hybrid
-    h, cs, cp, rho = 50.0, 3464.0, 6000.0, 2670.0
+    h = TPV3["dx"]
+    cs, cp, rho = TPV3["cs"], TPV3["cp"], TPV3["rho"]
     n1, n3 = 1024, 512
     dt = 0.3 * h / cp
     steps = args.n_cut or 1600
     x1 = (np.arange(n1) - n1 / 2 + 0.5) * h
     x3 = (np.arange(n3) - n3 / 2 + 0.5) * h
     X3, X1 = np.meshgrid(x3, x1, indexing="ij")
-    inside = (np.abs(X1) <= 15e3) & (np.abs(X3) <= 7.5e3)
-    patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
-    law = (np.where(inside, 0.677, 1e4), np.where(patch, 1.005 * 0.677 * 120e6, 70e6),
-           0.525, 0.4, 120e6)
+    law = tpv3_law(X1, X3)
     stations = {"x1=4.5km": (0.0, 4.5e3), "x1=7.5km": (0.0, 7.5e3), "x1=12km": (0.0, 12e3),
                 "x3=4.5km": (4.5e3, 0.0), "x3=6km": (6e3, 0.0)}
     idx = {k: (int(np.argmin(np.abs(x3 - a))), int(np.argmin(np.abs(x1 - b))))
@@ -558,7 +577,8 @@ def run_tpv3(args):
         g.close()
         return out
 
-    t_h, s_h, ms_h, clk_h = solve(lambda: Hybrid(n1, 4, n3, h, cs, cp, rho, dt, steps, "fp32"))
+    t_h, s_h, ms_h, clk_h = solve(lambda: Hybrid(n1, TPV3["strip_cells"], n3, h, cs, cp, rho, dt,
+                                                 steps, "fp32"))
     torch.cuda.empty_cache()
     t_p, s_p, ms_p, clk_p = solve(lambda: FaultSolver(n1, n3, n1 * h, n3 * h, cs, cp, rho, dt,
                                                       steps, "fp32", True))
