@@ -67,6 +67,24 @@ class FaultSolver:
         _, up, lo = B.sbim_fault_info(self.h)
         return up, (lo if lo.value else None)
 
+    def save(self):
+        """Checkpoint: both faces' u, v (host copies) and the half-spaces'
+        histories (sbim_save)."""
+        u, v = (x.cpu() for x in self.get_state())
+        up, lo = self.handles()
+        ck = {"u": u, "v": v, "up": B.sbim_save(up)}
+        if lo is not None:
+            ck["lo"] = B.sbim_save(lo)
+        return ck
+
+    def load(self, ck):
+        dev = self.stream.device
+        self.set_state(ck["u"].to(dev).contiguous(), ck["v"].to(dev).contiguous())
+        up, lo = self.handles()
+        B.sbim_load(up, ck["up"])
+        if lo is not None:
+            B.sbim_load(lo, ck["lo"])
+
     @property
     def steps(self):
         return B.sbim_fault_info(self.h)[0]

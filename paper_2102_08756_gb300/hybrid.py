@@ -83,6 +83,27 @@ class Hybrid:
         B.sbim_hybrid_fault_fields(self.h, *[o.data_ptr() for o in out])
         return tuple(out)
 
+    def save(self):
+        """Checkpoint of the coupled state: the slab's u, v, a (host copies) and
+        both half-spaces' histories (sbim_save).  The fault law is part of the
+        handle's parameters, not of the checkpoint; the slip is u+ - u-."""
+        u, v, a = (x.cpu() for x in self.get_state())
+        _, _, top, bot = B.sbim_hybrid_info(self.h)
+        ck = {"u": u, "v": v, "a": a}
+        if top.value:
+            ck["top"], ck["bot"] = B.sbim_save(top), B.sbim_save(bot)
+        return ck
+
+    def load(self, ck):
+        """Restore a checkpoint taken by ``save`` on a handle with the same
+        parameters; the run continues as the original did."""
+        dev = self.stream.device
+        self.set_state(*(ck[k].to(dev).contiguous() for k in ("u", "v", "a")))
+        _, _, top, bot = B.sbim_hybrid_info(self.h)
+        if top.value:
+            B.sbim_load(top, ck["top"])
+            B.sbim_load(bot, ck["bot"])
+
     @property
     def steps(self):
         return B.sbim_hybrid_info(self.h)[1]
