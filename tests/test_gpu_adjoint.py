@@ -103,3 +103,32 @@ def test_autograd_against_central_differences():
         fd = (J(u + eps * du, v + eps * dv) - J(u - eps * du, v - eps * dv)) / (2 * eps)
     an = float((gu * du).sum() + (gv * dv).sum())
     assert abs(float(fd) - an) < 1e-8 * abs(an), (float(fd), an)
+
+
+def test_dot_product_identity_at_the_gradient_configuration():
+    """The gradient configuration's full size: 256 x 256 boundary, 1024-lag
+    cutoff, 500 steps, FP32 history with Kahan sums and the default launch.
+    sum_n <tau_n, tau_bar_n> = sum_m <u_m, u_bar_m> + <v_m, v_bar_m> (far field
+    excluded) holds at any size; float rounding bounds the gap."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    n, steps = 256, 500
+    p = _params(n, n, 1024, 1, "fp32")
+    g = torch.Generator(device="cuda").manual_seed(11)
+    u = torch.randn((steps, 3, n, n), device="cuda", generator=g) * 1e-3
+    v = torch.randn((steps, 3, n, n), device="cuda", generator=g) * 1e-2
+    tb = torch.randn((steps, 3, n, n), device="cuda", generator=g)
+    fwd = SBIM(**p)
+    lhs = 0.0
+    for m in range(steps):
+        lhs += float((fwd.step(u[m], v[m]).double() * tb[m].double()).sum())
+    adj = SBIM(**p)
+    ub = torch.empty_like(u[0])
+    vb = torch.empty_like(u[0])
+    rhs = 0.0
+    for m in range(steps - 1, -1, -1):
+        adj.step_adjoint(tb[m], ub, vb)
+        rhs += float((u[m].double() * ub.double()).sum() + (v[m].double() * vb.double()).sum())
+    fwd.check()
+    adj.check()
+    scale = abs(lhs) + abs(rhs)
+    assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs)

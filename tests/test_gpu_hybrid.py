@@ -117,3 +117,43 @@ def test_gpu_sbim_boundaries_reproduce_an_unbounded_slab():
         ur = thick.get_state()[0].double().cpu().numpy()[pad:pad + n2 + 1]
         worst = max(worst, rel(ut, ur))
     assert worst < 0.08, worst
+
+
+def test_coupled_configuration_fp32_against_fp64_and_mirror_symmetry():
+    """The coupled configuration at full size: 512 x 16 x 512 slab, two 512²
+    half-spaces with 2000-lag cutoffs, TPV3 stresses.  Over the first 60 steps
+    of the rupture the FP32 path follows the FP64 path (the one checked against
+    the oracle at small sizes) within the rupture tolerance, and the FP64
+    solution keeps the mirror symmetry of the setup about the fault plane: the
+    top and bottom SBIM tractions are mirror images (tau_1,3 equal, tau_2
+    opposite), and the fault's normal traction perturbation stays at rounding."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n, n2, h, n_cut, steps = 512, 16, 100.0, 2000, 60
+    dt = 0.3 * h / CP
+    x = (np.arange(n) - n / 2 + 0.5) * h
+    X3, X1 = np.meshgrid(x, x, indexing="ij")
+    inside = (np.abs(X1) <= 15e3) & (np.abs(X3) <= 7.5e3)
+    patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
+    law = (np.where(inside, 0.677, 1e4), np.where(patch, 1.005 * 0.677 * 120e6, 70e6),
+           0.525, 0.4, 120e6)
+    runs = {}
+    for prec in ("fp64", "fp32"):
+        g = Hybrid(n, n2, n, h, CS, CP, RHO, dt, n_cut, prec)
+        g.set_fault(*law)
+        rates = []
+        for _ in range(steps):
+            g.step()
+            rates.append(g.fault_fields()[1].double())
+        top, bot = (t.double() for t in g.boundary_tractions())
+        trac = g.fault_fields()[2].double()
+        runs[prec] = (torch.stack(rates), top, bot, trac)
+        g.close()
+    r64, top, bot, trac = runs["fp64"]
+    r32 = runs["fp32"][0]
+    assert float(r64.abs().max()) > 1.0                          # the rupture runs
+    assert float((r32 - r64).abs().max()) < 3e-3 * float(r64.abs().max())
+    scale = float(top.abs().max())
+    assert float((top[0] - bot[0]).abs().max()) < 1e-9 * scale
+    assert float((top[2] - bot[2]).abs().max()) < 1e-9 * scale
+    assert float((top[1] + bot[1]).abs().max()) < 1e-9 * scale
+    assert float(trac[1].abs().max()) < 1e-9 * float(trac.abs().max())
