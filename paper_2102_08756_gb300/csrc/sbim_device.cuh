@@ -91,18 +91,18 @@ struct StoreBF16 {
   using real = float;
   using cplx = float2;
   using tab4 = float4;
-  // Read in two 8-byte chunks of 2 members each, so that a lag's values occupy
-  // half the registers of a whole-record read (the Kahan variants of the wider
-  // pipeline shapes otherwise spill).
-  static constexpr int kRecBytes = 16, kPlanes = LO ? 2 : 1, kChunks = 2, kChunkMembers = 2;
-  __device__ static void chunk_smem(const unsigned char* seg, int plane_bytes, int t, int r,
+  static constexpr int kRecBytes = 16, kPlanes = LO ? 2 : 1, kChunks = 1, kChunkMembers = 4;
+  __device__ static void chunk_smem(const unsigned char* seg, int plane_bytes, int t, int,
                                     cplx* out) {
-    const uint2 hi = *reinterpret_cast<const uint2*>(seg + t * kRecBytes + r * 8);
+    const uint4 hi = *reinterpret_cast<const uint4*>(seg + t * kRecBytes);
     out[0] = unpack_bf16(hi.x); out[1] = unpack_bf16(hi.y);
+    out[2] = unpack_bf16(hi.z); out[3] = unpack_bf16(hi.w);
     if (LO) {
-      const uint2 lo = *reinterpret_cast<const uint2*>(seg + plane_bytes + t * kRecBytes + r * 8);
+      const uint4 lo = *reinterpret_cast<const uint4*>(seg + plane_bytes + t * kRecBytes);
       const float2 l0 = unpack_bf16(lo.x), l1 = unpack_bf16(lo.y);
+      const float2 l2 = unpack_bf16(lo.z), l3 = unpack_bf16(lo.w);
       out[0].x += l0.x; out[0].y += l0.y; out[1].x += l1.x; out[1].y += l1.y;
+      out[2].x += l2.x; out[2].y += l2.y; out[3].x += l3.x; out[3].y += l3.y;
     }
   }
   __device__ static void load(const void* h, long long rec, long long plane, cplx D[4]) {
