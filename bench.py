@@ -650,11 +650,17 @@ def run_ensemble(args):
             x.set_fault(0.677, tau0, 0.525, sc["Dc"], 120e6)
             members.append(x)
         b = B.sbim_hybrid_batch_create([x.h for x in members])
+        if args.variant >= 1:
+            B.sbim_hybrid_batch_set_conv_config(b, args.variant, args.lags_per_cta)
         B.sbim_hybrid_batch_capture(b)
         K, W = args.steps, args.warmup
         for _ in range(max(sc["n_cut"] for sc in scen) + W):
             B.sbim_hybrid_batch_replay(b)
         stream.synchronize()
+        tuned = None
+        if args.tune:
+            from paper_2102_08756_gb300.tune import autotune_hybrid_batch
+            tuned = autotune_hybrid_batch(b, stream)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
@@ -681,6 +687,8 @@ def run_ensemble(args):
         "sbim_macs_per_s": macs / (ms * 1e-3), "hbm_gbs_history": hist_bytes / (ms * 1e-3) / 1e9,
         "max_slip_rate_m_s": peak_rate, "clocks": clk.summary(),
     }
+    if tuned is not None:
+        line["autotune"] = tuned
     print(json.dumps(line), flush=True)
 
 

@@ -314,6 +314,14 @@ int sbim_batch_step(sbim_batch b, const void* const* u, const void* const* v, vo
 int sbim_batch_capture(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
 int sbim_batch_replay(sbim_batch b);
 
+/*
+ * sbim_batch_set_conv_config -- launch of the batch's persistent convolution:
+ * TMA pipeline shape (1..3, as in sbim_set_conv_config) and lags per work item
+ * (0: 256).  Results do not depend on it beyond float rounding.  Drops a
+ * captured graph: capture again before replaying.
+ */
+int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
+
 /* sbim_batch_member -- the handle of member i (owned by the batch). */
 int sbim_batch_member(sbim_batch b, int i, sbim_handle* h);
 
@@ -483,6 +491,9 @@ int sbim_hybrid_batch_create(sbim_hybrid_batch* out, int nb, const sbim_hybrid* 
 int sbim_hybrid_batch_step(sbim_hybrid_batch b);
 int sbim_hybrid_batch_capture(sbim_hybrid_batch b);
 int sbim_hybrid_batch_replay(sbim_hybrid_batch b);
+/* sbim_hybrid_batch_set_conv_config -- as sbim_batch_set_conv_config for the
+ * batch's 2 nb half-spaces; drops a captured graph. */
+int sbim_hybrid_batch_set_conv_config(sbim_hybrid_batch b, int shape, int lags_per_item);
 int sbim_hybrid_batch_destroy(sbim_hybrid_batch b);
 
 /* sbim_destroy -- free everything the handle owns; NULL is accepted. */

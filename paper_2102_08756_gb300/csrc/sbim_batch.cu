@@ -59,8 +59,57 @@ void brelease(sbim_batch_ctx* b) {
   delete b;
 }
 
-// Lag chunks of 256 lags for every member: items of comparable cost.
+// Default launch of the persistent kernel: lag chunks of 256 lags for every
+// member (items of comparable cost); pipeline shape 3 for float history
+// (2 stages x 4 lags, 2 CTAs/SM) and shape 1 for bf16 (4 x 2 / 8 x 2, 2 CTAs/SM).
+// sbim_batch_set_conv_config changes both.
 constexpr int kBatchLags = 256;
+constexpr int kBatchShapeF32 = 3;
+constexpr int kBatchShapeBF16 = 1;
+
+void drop_graph(sbim_batch_ctx* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// (Re)configure the members' lag chunking and the kernel shape, and upload the
+// per-member arguments and item / tile prefix sums.
+int configure(sbim_batch_ctx* b, int shape, int lags) {
+  for (int i = 0; i < b->nb; ++i) {
+    const int rc = sbim_set_conv_config(b->h[i], shape, lags);
+    if (rc != SBIM_OK) return rc;
+  }
+  BCU(sbim::prepare_conv_tma(b->prec, b->kahan, shape));
+  b->shape = shape;
+  std::vector<sbim::StepArgs> args(b->nb);
+  std::vector<int> items(b->nb + 1, 0), tiles(b->nb + 1, 0);
+  for (int i = 0; i < b->nb; ++i) {
+    args[i] = sbim::handle_step_args(b->h[i]);
+    const int t = args[i].n_orb_pad / sbim::kOrbitTile;
+    tiles[i + 1] = tiles[i] + t;
+    items[i + 1] = items[i] + t * args[i].nchunks;
+  }
+  b->total_items = items[b->nb];
+  b->total_tiles = tiles[b->nb];
+  if (!b->d_args) BCU(cudaMalloc(&b->d_args, b->nb * sizeof(sbim::StepArgs)));
+  if (!b->d_item_prefix) BCU(cudaMalloc(&b->d_item_prefix, (b->nb + 1) * sizeof(int)));
+  if (!b->d_tile_prefix) BCU(cudaMalloc(&b->d_tile_prefix, (b->nb + 1) * sizeof(int)));
+  if (!b->d_counter) BCU(cudaMalloc(&b->d_counter, sizeof(int)));
+  BCU(cudaMemcpyAsync(b->d_args, args.data(), b->nb * sizeof(sbim::StepArgs),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemcpyAsync(b->d_item_prefix, items.data(), (b->nb + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemcpyAsync(b->d_tile_prefix, tiles.data(), (b->nb + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaStreamSynchronize(b->stream));
+  int dev = 0, sms = 148;
+  BCU(cudaGetDevice(&dev));
+  BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape);
+  return SBIM_OK;
+}
 
 int setup(sbim_batch_ctx* b) {
   int prec0 = 0, kahan0 = 0;
@@ -77,41 +126,8 @@ int setup(sbim_batch_ctx* b) {
     }
     if (prec == SBIM_FP64) return bfail(SBIM_ERR_ARG, "batches use float or bf16 history");
   }
-  // pipeline shape of the persistent kernel: the ones that fit its register
-  // budget without spilling (float: 2 stages x 4 lags; bf16: 4 x 2 / 8 x 2)
-  const int shape = prec0 == SBIM_FP32 ? 3 : 1;
-  for (int i = 0; i < b->nb; ++i) {
-    const int rc = sbim_set_conv_config(b->h[i], shape, kBatchLags);
-    if (rc != SBIM_OK) return rc;
-  }
-  BCU(sbim::prepare_conv_tma(prec0, kahan0, shape));
-  b->prec = prec0; b->kahan = kahan0; b->shape = shape; b->stream = (cudaStream_t)st0;
-  std::vector<sbim::StepArgs> args(b->nb);
-  std::vector<int> items(b->nb + 1, 0), tiles(b->nb + 1, 0);
-  for (int i = 0; i < b->nb; ++i) {
-    args[i] = sbim::handle_step_args(b->h[i]);
-    const int t = args[i].n_orb_pad / sbim::kOrbitTile;
-    tiles[i + 1] = tiles[i] + t;
-    items[i + 1] = items[i] + t * args[i].nchunks;
-  }
-  b->total_items = items[b->nb];
-  b->total_tiles = tiles[b->nb];
-  BCU(cudaMalloc(&b->d_args, b->nb * sizeof(sbim::StepArgs)));
-  BCU(cudaMalloc(&b->d_item_prefix, (b->nb + 1) * sizeof(int)));
-  BCU(cudaMalloc(&b->d_tile_prefix, (b->nb + 1) * sizeof(int)));
-  BCU(cudaMalloc(&b->d_counter, sizeof(int)));
-  BCU(cudaMemcpyAsync(b->d_args, args.data(), b->nb * sizeof(sbim::StepArgs),
-                      cudaMemcpyHostToDevice, b->stream));
-  BCU(cudaMemcpyAsync(b->d_item_prefix, items.data(), (b->nb + 1) * sizeof(int),
-                      cudaMemcpyHostToDevice, b->stream));
-  BCU(cudaMemcpyAsync(b->d_tile_prefix, tiles.data(), (b->nb + 1) * sizeof(int),
-                      cudaMemcpyHostToDevice, b->stream));
-  BCU(cudaStreamSynchronize(b->stream));
-  int dev = 0, sms = 148;
-  BCU(cudaGetDevice(&dev));
-  BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape);
-  return SBIM_OK;
+  b->prec = prec0; b->kahan = kahan0; b->stream = (cudaStream_t)st0;
+  return configure(b, prec0 == SBIM_FP32 ? kBatchShapeF32 : kBatchShapeBF16, kBatchLags);
 }
 
 // Enqueue one step of every member (pointer arrays are host arrays of device pointers).
@@ -159,6 +175,9 @@ int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n) {
 }
 int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau) {
   return enqueue(b, u, v, tau);
+}
+int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
+  return sbim_batch_set_conv_config(b, shape, lags_per_item);
 }
 void batch_advance(sbim_batch b) {
   for (sbim_handle x : b->h) handle_advance(x);
@@ -236,6 +255,14 @@ int sbim_batch_replay(sbim_batch b) {
   BCU(cudaGraphLaunch(b->exec, b->stream));
   sbim::batch_advance(b);
   return SBIM_OK;
+}
+
+int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
+  if (!b) return bfail(SBIM_ERR_ARG, "NULL batch");
+  if (shape < 1 || shape > 3) return bfail(SBIM_ERR_ARG, "shape must be 1..3");
+  if (lags_per_item < 0) return bfail(SBIM_ERR_ARG, "lags_per_item must be >= 0");
+  drop_graph(b);
+  return configure(b, shape, lags_per_item ? lags_per_item : kBatchLags);
 }
 
 int sbim_batch_member(sbim_batch b, int i, sbim_handle* h) {

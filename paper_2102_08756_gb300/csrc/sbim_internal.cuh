@@ -110,6 +110,7 @@ int handle_shape(sbim_handle h, int* precision, int* kahan, int* variant, void**
 
 // Batch over existing handles (not owned); enqueue one step / advance the counters.
 int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n);
+int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
 int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
 void batch_advance(sbim_batch b);
 

@@ -64,6 +64,8 @@ def lib():
     L.sbim_fault_fields.argtypes = [vp, vp, vp, vp]
     L.sbim_fault_info.argtypes = [vp, ctypes.POINTER(ll), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.sbim_fault_destroy.argtypes = [vp]
+    L.sbim_batch_set_conv_config.argtypes = [vp, i, i]
+    L.sbim_hybrid_batch_set_conv_config.argtypes = [vp, i, i]
     L.sbim_hybrid_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, d, d, d, i, i, i, i, vp]
     L.sbim_hybrid_set_fault.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), d, d, d]
     L.sbim_hybrid_set_state.argtypes = [vp, vp, vp, vp]
@@ -232,6 +234,14 @@ def sbim_batch_create(n1, n3, L1, L3, cs, cp, rho, dt, n_cut, side, precision, k
                                    *[d.ctypes.data for d in dbls], ints[2].ctypes.data,
                                    ints[3].ctypes.data, precision, kahan, stream))
     return b
+
+
+def sbim_batch_set_conv_config(b, shape, lags_per_item=0):
+    _check(lib().sbim_batch_set_conv_config(b, int(shape), int(lags_per_item)))
+
+
+def sbim_hybrid_batch_set_conv_config(b, shape, lags_per_item=0):
+    _check(lib().sbim_hybrid_batch_set_conv_config(b, int(shape), int(lags_per_item)))
 
 
 def sbim_batch_step(b, u_ptrs, v_ptrs, tau_ptrs):

@@ -61,3 +61,32 @@ def autotune(h, u, v, steps=6, chunkings=None, cache=None, verbose=False):
         with open(cache, "w") as f:
             json.dump(db, f, indent=1)
     return best, table
+
+
+def autotune_hybrid_batch(b, stream, shapes=(1, 2, 3), lags=(128, 256, 512, 1024), steps=4):
+    """Time whole captured ensemble steps of a hybrid batch for every (pipeline
+    shape, lags per work item) of the persistent convolution and keep the
+    fastest (the batch is left captured with it).  Each trial advances the
+    ensemble by ``steps + 1`` steps."""
+    from . import sbim as B
+    table = []
+    for shape in shapes:
+        for lpi in lags:
+            try:
+                B.sbim_hybrid_batch_set_conv_config(b, shape, lpi)
+                B.sbim_hybrid_batch_capture(b)
+            except RuntimeError:
+                continue
+            B.sbim_hybrid_batch_replay(b)              # warm-up of this launch
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                B.sbim_hybrid_batch_replay(b)
+            e1.record(stream)
+            stream.synchronize()
+            table.append({"shape": shape, "lags_per_item": lpi, "step_ms": e0.elapsed_time(e1) / steps})
+    best = min(table, key=lambda r: r["step_ms"])
+    B.sbim_hybrid_batch_set_conv_config(b, best["shape"], best["lags_per_item"])
+    B.sbim_hybrid_batch_capture(b)
+    return {"best": best, "trials": table}

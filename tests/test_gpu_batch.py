@@ -43,16 +43,21 @@ def _fields(hist, m):
     return u, v
 
 
-def test_batch_equals_members_stepped_alone():
+@pytest.mark.parametrize("shape,lags", [(None, None), (1, 128), (2, 64)])
+def test_batch_equals_members_stepped_alone(shape, lags):
+    """Default launch (pipeline shape 3, 256-lag items) and two others set with
+    sbim_batch_set_conv_config."""
     from paper_2102_08756_gb300.sbim import SBIM
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         B, b, hist, dt = _setup(stream)
+        if shape is not None:
+            B.sbim_batch_set_conv_config(b, shape, lags)
         alone = []
         for (a, c, n_cut, side) in MEMBERS:
             h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "fp32", True,
                      stream=stream)
-            h.set_conv_config(3, 256)
+            h.set_conv_config(3, 256) if shape is None else h.set_conv_config(shape, lags)
             alone.append(h)
         oracles = [SBIMOracle(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side)
                    for (a, c, n_cut, side) in MEMBERS[:2]]
@@ -106,7 +111,8 @@ def test_graph_replay_equals_direct_steps():
         B.sbim_batch_destroy(b2)
 
 
-def test_hybrid_ensemble_batch_and_graph():
+@pytest.mark.parametrize("shape,lags", [(None, None), (1, 16)])
+def test_hybrid_ensemble_batch_and_graph(shape, lags):
     """Three coupled scenarios with different grids, slab thicknesses, fault laws
     and cutoffs: the ensemble step (one batched SBIM launch for the six
     half-spaces) and its CUDA-graph replay equal the scenarios stepped alone."""
@@ -131,10 +137,16 @@ def test_hybrid_ensemble_batch_and_graph():
         alone, batched, graphed = make(), make(), make()
         for x in alone:
             _, _, top, bot = B.sbim_hybrid_info(x.h)
-            B.sbim_set_conv_config(top, 3, 256)
-            B.sbim_set_conv_config(bot, 3, 256)
+            B.sbim_set_conv_config(top, shape or 3, lags or 256)
+            B.sbim_set_conv_config(bot, shape or 3, lags or 256)
         b1 = B.sbim_hybrid_batch_create([x.h for x in batched])
         b2 = B.sbim_hybrid_batch_create([x.h for x in graphed])
+        if shape is not None:
+            B.sbim_hybrid_batch_set_conv_config(b1, shape, lags)
+            B.sbim_hybrid_batch_capture(b2)                 # dropped by the next call
+            B.sbim_hybrid_batch_set_conv_config(b2, shape, lags)
+            with pytest.raises(B.SBIMError):
+                B.sbim_hybrid_batch_replay(b2)
         B.sbim_hybrid_batch_capture(b2)
         for step in range(40):
             for x in alone:
