@@ -59,12 +59,13 @@ void brelease(sbim_batch_ctx* b) {
   delete b;
 }
 
-// Default launch of the persistent kernel: lag chunks of 256 lags for every
-// member (items of comparable cost); pipeline shape 3 for float history
-// (2 stages x 4 lags, 2 CTAs/SM) and shape 1 for bf16 (4 x 2 / 8 x 2, 2 CTAs/SM).
-// sbim_batch_set_conv_config changes both.
-constexpr int kBatchLags = 256;
-constexpr int kBatchShapeF32 = 3;
+// Default launch of the persistent kernel: work items of up to 1024 lags of one
+// orbit tile, and pipeline shape 1 (4 stages x 2 lags, 2 CTAs/SM; 8 x 2 for bf16
+// hi-only), the fastest of the shapes and item sizes the batch autotuner timed on
+// GB300 for a 32-scenario coupled ensemble (25.2 ms per step, against 26.0 ms
+// for shape 3 with 256-lag items).  sbim_batch_set_conv_config changes both.
+constexpr int kBatchLags = 1024;
+constexpr int kBatchShapeF32 = 1;
 constexpr int kBatchShapeBF16 = 1;
 
 void drop_graph(sbim_batch_ctx* b) {

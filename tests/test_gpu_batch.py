@@ -43,9 +43,9 @@ def _fields(hist, m):
     return u, v
 
 
-@pytest.mark.parametrize("shape,lags", [(None, None), (1, 128), (2, 64)])
+@pytest.mark.parametrize("shape,lags", [(None, None), (3, 256), (2, 64)])
 def test_batch_equals_members_stepped_alone(shape, lags):
-    """Default launch (pipeline shape 3, 256-lag items) and two others set with
+    """Default launch (pipeline shape 1, 1024-lag items) and two others set with
     sbim_batch_set_conv_config."""
     from paper_2102_08756_gb300.sbim import SBIM
     stream = torch.cuda.Stream()
@@ -57,7 +57,7 @@ def test_batch_equals_members_stepped_alone(shape, lags):
         for (a, c, n_cut, side) in MEMBERS:
             h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "fp32", True,
                      stream=stream)
-            h.set_conv_config(3, 256) if shape is None else h.set_conv_config(shape, lags)
+            h.set_conv_config(1, 1024) if shape is None else h.set_conv_config(shape, lags)
             alone.append(h)
         oracles = [SBIMOracle(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side)
                    for (a, c, n_cut, side) in MEMBERS[:2]]
@@ -111,7 +111,7 @@ def test_graph_replay_equals_direct_steps():
         B.sbim_batch_destroy(b2)
 
 
-@pytest.mark.parametrize("shape,lags", [(None, None), (1, 16)])
+@pytest.mark.parametrize("shape,lags", [(None, None), (3, 16)])
 def test_hybrid_ensemble_batch_and_graph(shape, lags):
     """Three coupled scenarios with different grids, slab thicknesses, fault laws
     and cutoffs: the ensemble step (one batched SBIM launch for the six
@@ -137,8 +137,8 @@ def test_hybrid_ensemble_batch_and_graph(shape, lags):
         alone, batched, graphed = make(), make(), make()
         for x in alone:
             _, _, top, bot = B.sbim_hybrid_info(x.h)
-            B.sbim_set_conv_config(top, shape or 3, lags or 256)
-            B.sbim_set_conv_config(bot, shape or 3, lags or 256)
+            B.sbim_set_conv_config(top, shape or 1, lags or 1024)
+            B.sbim_set_conv_config(bot, shape or 1, lags or 1024)
         b1 = B.sbim_hybrid_batch_create([x.h for x in batched])
         b2 = B.sbim_hybrid_batch_create([x.h for x in graphed])
         if shape is not None:
