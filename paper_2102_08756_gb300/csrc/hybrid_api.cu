@@ -148,9 +148,13 @@ const sbim::fem::Stencil<double>& stencil_of(const sbim_hybrid_ctx* c, double) {
 
 // Stage (1): FE predictor.
 template <class R>
-int stage_predict(sbim_hybrid_ctx* c) {
-  HCU(sbim::fem::predict<R>((R*)c->u, (R*)c->v, (const R*)c->a, c->elems(), (R)c->dt, c->stream));
+int stage_predict(sbim_hybrid_ctx* c, cudaStream_t st) {
+  HCU(sbim::fem::predict<R>((R*)c->u, (R*)c->v, (const R*)c->a, c->elems(), (R)c->dt, st));
   return SBIM_OK;
+}
+template <class R>
+int stage_predict(sbim_hybrid_ctx* c) {
+  return stage_predict<R>(c, c->stream);
 }
 
 // Boundary layers handed to the SBIM half-spaces (top: last layer, bottom: first).
@@ -165,8 +169,7 @@ void boundary_ptrs(sbim_hybrid_ctx* c, const void** u_top, const void** v_top,
 
 // Stages (4)-(7): forces, fault traction, acceleration increment, correction.
 template <class R>
-int stage_finish(sbim_hybrid_ctx* c, const void* src) {
-  cudaStream_t st = c->stream;
+int stage_finish(sbim_hybrid_ctx* c, const void* src, cudaStream_t st) {
   const R dt = (R)c->dt;
   const long long n = c->elems();
   R* u = (R*)c->u;
@@ -188,6 +191,10 @@ int stage_finish(sbim_hybrid_ctx* c, const void* src) {
   }
   HCU(sbim::fem::correct<R>(v, a, an, n, dt, st));
   return SBIM_OK;
+}
+template <class R>
+int stage_finish(sbim_hybrid_ctx* c, const void* src) {
+  return stage_finish<R>(c, src, c->stream);
 }
 
 template <class R>
@@ -474,10 +481,13 @@ int sbim_hybrid_batch_create(sbim_hybrid_batch* out, int nb, const sbim_hybrid* 
 
 namespace {
 int hbatch_enqueue(sbim_hybrid_batch b) {
-  for (sbim_hybrid x : b->m) {
-    const int rc = stage_predict<float>(x);
-    if (rc != SBIM_OK) return rc;
-  }
+  // the members' FE stages run on the batch's side streams (member k on side
+  // stream k mod 8), forked from and joined back into the shared stream
+  int rc = sbim::batch_fork(b->sb);
+  for (size_t k = 0; k < b->m.size() && rc == SBIM_OK; ++k)
+    rc = stage_predict<float>(b->m[k], sbim::batch_side(b->sb, (int)k));
+  if (rc == SBIM_OK) rc = sbim::batch_join(b->sb);
+  if (rc != SBIM_OK) return rc;
   std::vector<const void*> u, v;
   std::vector<void*> tau;
   for (sbim_hybrid x : b->m) {
@@ -486,13 +496,12 @@ int hbatch_enqueue(sbim_hybrid_batch b) {
     u.push_back(ut); v.push_back(vt); tau.push_back(x->tau_top);
     u.push_back(ub); v.push_back(vb); tau.push_back(x->tau_bot);
   }
-  int rc = sbim::batch_enqueue(b->sb, u.data(), v.data(), tau.data());
-  if (rc != SBIM_OK) return rc;
-  for (sbim_hybrid x : b->m) {
-    rc = stage_finish<float>(x, nullptr);
-    if (rc != SBIM_OK) return rc;
-  }
-  return SBIM_OK;
+  rc = sbim::batch_enqueue(b->sb, u.data(), v.data(), tau.data());
+  if (rc == SBIM_OK) rc = sbim::batch_fork(b->sb);
+  for (size_t k = 0; k < b->m.size() && rc == SBIM_OK; ++k)
+    rc = stage_finish<float>(b->m[k], nullptr, sbim::batch_side(b->sb, (int)k));
+  if (rc == SBIM_OK) rc = sbim::batch_join(b->sb);
+  return rc;
 }
 void hbatch_advance(sbim_hybrid_batch b) {
   sbim::batch_advance(b->sb);

@@ -466,27 +466,37 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 StepArgs handle_step_args(sbim_handle h) { return step_args(h); }
 
-int handle_fft_forward(sbim_handle c, const void* u) {
+// The batch drivers run members' small stages on side streams: the plans are
+// pointed at the given stream for the call and back at the handle's after it.
+int handle_fft_forward(sbim_handle c, const void* u, cudaStream_t st) {
+  if (st != c->stream) CF(cufftSetStream(c->plan_fwd, st));
+  cufftResult r;
   if (c->prec == SBIM_FP64)
-    CF(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)u, (cufftDoubleComplex*)c->d_uhat));
+    r = cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)u, (cufftDoubleComplex*)c->d_uhat);
   else
-    CF(cufftExecR2C(c->plan_fwd, (cufftReal*)u, (cufftComplex*)c->d_uhat));
+    r = cufftExecR2C(c->plan_fwd, (cufftReal*)u, (cufftComplex*)c->d_uhat);
+  if (st != c->stream) CF(cufftSetStream(c->plan_fwd, c->stream));
+  CF(r);
   return SBIM_OK;
 }
 
-int handle_fft_inverse(sbim_handle c) {
+int handle_fft_inverse(sbim_handle c, cudaStream_t st) {
+  if (st != c->stream) CF(cufftSetStream(c->plan_inv, st));
+  cufftResult r;
   if (c->prec == SBIM_FP64)
-    CF(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)c->d_s));
+    r = cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)c->d_fhat, (cufftDoubleReal*)c->d_s);
   else
-    CF(cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)c->d_s));
+    r = cufftExecC2R(c->plan_inv, (cufftComplex*)c->d_fhat, (cufftReal*)c->d_s);
+  if (st != c->stream) CF(cufftSetStream(c->plan_inv, c->stream));
+  CF(r);
   return SBIM_OK;
 }
 
-int handle_epilogue(sbim_handle c, const void* v, void* tau) {
+int handle_epilogue(sbim_handle c, const void* v, void* tau, cudaStream_t st) {
   const double k = c->side * c->mu / c->cs;
   const double coef[3] = {k, k * c->eta, k};
   CU(launch_epilogue(c->prec, c->d_s, v, tau, (long long)c->n1 * c->n3, coef, c->tau_inf,
-                     c->d_step, c->stream));
+                     c->d_step, st));
   return SBIM_OK;
 }
 

@@ -25,6 +25,11 @@ struct sbim_batch_ctx {
   int total_items = 0, total_tiles = 0, ctas = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // side streams for the members' small stages (FFTs, epilogues): they run
+  // concurrently instead of as one serial chain of small launches
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -49,6 +54,9 @@ int bfail(int code, const char* fmt, ...) {
 
 void brelease(sbim_batch_ctx* b) {
   if (!b) return;
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  for (cudaStream_t x : b->side) cudaStreamDestroy(x);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->owns)
@@ -65,6 +73,23 @@ void brelease(sbim_batch_ctx* b) {
 // GB300 for a 32-scenario coupled ensemble (25.2 ms per step, against 26.0 ms
 // for shape 3 with 256-lag items).  sbim_batch_set_conv_config changes both.
 constexpr int kBatchLags = 1024;
+constexpr int kSideStreams = 8;
+
+int fork(sbim_batch_ctx* b) {
+  BCU(cudaEventRecord(b->fork_ev, b->stream));
+  for (cudaStream_t x : b->side) BCU(cudaStreamWaitEvent(x, b->fork_ev, 0));
+  return SBIM_OK;
+}
+
+int join(sbim_batch_ctx* b) {
+  for (size_t i = 0; i < b->side.size(); ++i) {
+    BCU(cudaEventRecord(b->joins[i], b->side[i]));
+    BCU(cudaStreamWaitEvent(b->stream, b->joins[i], 0));
+  }
+  return SBIM_OK;
+}
+
+cudaStream_t side_of(sbim_batch_ctx* b, int i) { return b->side[i % b->side.size()]; }
 constexpr int kBatchShapeF32 = 1;
 constexpr int kBatchShapeBF16 = 1;
 
@@ -128,15 +153,26 @@ int setup(sbim_batch_ctx* b) {
     if (prec == SBIM_FP64) return bfail(SBIM_ERR_ARG, "batches use float or bf16 history");
   }
   b->prec = prec0; b->kahan = kahan0; b->stream = (cudaStream_t)st0;
+  const int k = b->nb < kSideStreams ? b->nb : kSideStreams;
+  BCU(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+  for (int i = 0; i < k; ++i) {
+    cudaStream_t x = nullptr;
+    cudaEvent_t e = nullptr;
+    BCU(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    b->side.push_back(x);
+    BCU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->joins.push_back(e);
+  }
   return configure(b, prec0 == SBIM_FP32 ? kBatchShapeF32 : kBatchShapeBF16, kBatchLags);
 }
 
 // Enqueue one step of every member (pointer arrays are host arrays of device pointers).
 int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void* const* tau) {
-  for (int i = 0; i < b->nb; ++i) {
-    const int rc = sbim::handle_fft_forward(b->h[i], u[i]);
-    if (rc != SBIM_OK) return rc;
-  }
+  int rc = fork(b);
+  for (int i = 0; i < b->nb && rc == SBIM_OK; ++i)
+    rc = sbim::handle_fft_forward(b->h[i], u[i], side_of(b, i));
+  if (rc == SBIM_OK) rc = join(b);
+  if (rc != SBIM_OK) return rc;
   BCU(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
   sbim::BatchLaunch bl;
   bl.args = b->d_args;
@@ -148,12 +184,13 @@ int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void*
   const sbim::StepArgs a0 = sbim::handle_step_args(b->h[0]);
   BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl));
   BCU(sbim::launch_assemble_batch(bl, b->total_tiles, b->prec, b->kahan, b->stream));
-  for (int i = 0; i < b->nb; ++i) {
-    int rc = sbim::handle_fft_inverse(b->h[i]);
-    if (rc == SBIM_OK) rc = sbim::handle_epilogue(b->h[i], v[i], tau[i]);
-    if (rc != SBIM_OK) return rc;
+  rc = fork(b);
+  for (int i = 0; i < b->nb && rc == SBIM_OK; ++i) {
+    rc = sbim::handle_fft_inverse(b->h[i], side_of(b, i));
+    if (rc == SBIM_OK) rc = sbim::handle_epilogue(b->h[i], v[i], tau[i], side_of(b, i));
   }
-  return SBIM_OK;
+  if (rc == SBIM_OK) rc = join(b);
+  return rc;
 }
 
 }  // namespace
@@ -177,6 +214,9 @@ int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n) {
 int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau) {
   return enqueue(b, u, v, tau);
 }
+int batch_fork(sbim_batch b) { return fork(b); }
+cudaStream_t batch_side(sbim_batch b, int i) { return side_of(b, i); }
+int batch_join(sbim_batch b) { return join(b); }
 int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
   return sbim_batch_set_conv_config(b, shape, lags_per_item);
 }

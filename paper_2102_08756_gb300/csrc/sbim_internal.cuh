@@ -102,15 +102,21 @@ void set_last_error(const char* msg);
 // Stages of one handle's update, for drivers that batch the convolution of
 // several handles (each returns an sbim_status).
 StepArgs handle_step_args(sbim_handle h);
-int handle_fft_forward(sbim_handle h, const void* u);
-int handle_fft_inverse(sbim_handle h);
-int handle_epilogue(sbim_handle h, const void* v, void* tau);
+int handle_fft_forward(sbim_handle h, const void* u, cudaStream_t st);
+int handle_fft_inverse(sbim_handle h, cudaStream_t st);
+int handle_epilogue(sbim_handle h, const void* v, void* tau, cudaStream_t st);
 void handle_advance(sbim_handle h);
 int handle_shape(sbim_handle h, int* precision, int* kahan, int* variant, void** stream);
 
 // Batch over existing handles (not owned); enqueue one step / advance the counters.
 int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n);
 int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
+// Fork / join of the batch's side streams around per-member stages: after
+// batch_fork, work on batch_side(b, i) follows everything enqueued on the
+// batch's stream; batch_join makes the batch's stream wait for all of it.
+int batch_fork(sbim_batch b);
+cudaStream_t batch_side(sbim_batch b, int i);
+int batch_join(sbim_batch b);
 int batch_enqueue(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
 void batch_advance(sbim_batch b);
 
