@@ -79,17 +79,13 @@ __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>&
 }
 
 // The stencil -K x for every node of one (i1, i3) column, marching up the node
-// layers with register windows of x.  Each layer of x is loaded once per column
-// (27 values), not once per neighbouring node layer.  A layer's element blocks
-// below (down) and above (up) exist unless they cross the split fault plane or
-// the slab's faces.  Per node, epi(l, q0, down, up, F) finishes.
-//   float: three windows (layers l-1, l, l+1) rotating roles; the window of layer
-//     l-1 is reloaded with layer l+2 right after the blocks below node l are
-//     applied, so that load is in flight during the blocks above node l and the
-//     blocks below node l+1.
-//   double: two windows (the three would not fit in registers): the window of
-//     layer l-1 is reloaded with layer l+1 between the blocks below and above.
-// The blocks below and above accumulate separately and are added at the end.
+// layers with two register windows: at layer l one holds layer l-1 and the other
+// layer l; after the blocks below the node are applied, the first is reloaded
+// with layer l+1 for the blocks above, and the two swap roles for layer l+1.
+// Each layer of x is loaded once per column (27 values), not once per
+// neighbouring node layer.  A layer's element blocks below (down) and above (up)
+// exist unless they cross the split fault plane or the slab's faces.  Per node,
+// epi(l, q0, down, up, F) finishes.
 template <class R, class Epi>
 __device__ __forceinline__ void stencil_column(const R* __restrict__ x, const MeshArgs& g,
                                                const Stencil<R>& S, int i1, int i3, Epi epi) {
@@ -109,48 +105,22 @@ __device__ __forceinline__ void stencil_column(const R* __restrict__ x, const Me
   const long long q0 = (long long)i3 * g.n1 + i1;
   const long long layer = 3 * plane;
   int l = 0;
-  auto finish = [&](bool down, bool up, R (&Fd)[3], R (&Fu)[3]) {
-    R F[3] = {Fd[0] + Fu[0], Fd[1] + Fu[1], Fd[2] + Fu[2]};
+  auto node = [&](Window<R>& prev, Window<R>& cur) {
+    const bool down = l > 0 && !(g.fault && l == g.f + 1);
+    const bool up = l < g.L - 1 && !(g.fault && l == g.f);
+    R F[3] = {(R)0, (R)0, (R)0};
+    if (down) apply_side<0>(S, prev, cur, F);
+    if (l + 1 < g.L) load_window(x + (l + 1) * layer, plane, q, prev);   // prev := layer l+1
+    if (up) apply_side<1>(S, cur, prev, F);
     epi(l, q0, down, up, F);
     ++l;
   };
-  if constexpr (sizeof(R) == 4) {
-    auto node = [&](Window<R>& prev, Window<R>& cur, Window<R>& next) {
-      const bool down = l > 0 && !(g.fault && l == g.f + 1);
-      const bool up = l < g.L - 1 && !(g.fault && l == g.f);
-      R Fd[3] = {(R)0, (R)0, (R)0}, Fu[3] = {(R)0, (R)0, (R)0};
-      if (down) apply_side<0>(S, prev, cur, Fd);
-      if (l + 2 < g.L) load_window(x + (l + 2) * layer, plane, q, prev);   // prev := layer l+2
-      if (up) apply_side<1>(S, cur, next, Fu);
-      finish(down, up, Fd, Fu);
-    };
-    Window<R> A, B, C;
-    load_window(x, plane, q, B);
-    if (g.L > 1) load_window(x + layer, plane, q, C);
-    while (l < g.L) {
-      node(A, B, C);
-      if (l >= g.L) break;
-      node(B, C, A);
-      if (l >= g.L) break;
-      node(C, A, B);
-    }
-  } else {
-    auto node = [&](Window<R>& prev, Window<R>& cur) {
-      const bool down = l > 0 && !(g.fault && l == g.f + 1);
-      const bool up = l < g.L - 1 && !(g.fault && l == g.f);
-      R Fd[3] = {(R)0, (R)0, (R)0}, Fu[3] = {(R)0, (R)0, (R)0};
-      if (down) apply_side<0>(S, prev, cur, Fd);
-      if (l + 1 < g.L) load_window(x + (l + 1) * layer, plane, q, prev);   // prev := layer l+1
-      if (up) apply_side<1>(S, cur, prev, Fu);
-      finish(down, up, Fd, Fu);
-    };
-    Window<R> A, B;
-    load_window(x, plane, q, B);
-    while (l < g.L) {
-      node(A, B);
-      if (l >= g.L) break;
-      node(B, A);
-    }
+  Window<R> A, B;
+  load_window(x, plane, q, B);
+  while (l < g.L) {
+    node(A, B);
+    if (l >= g.L) break;
+    node(B, A);
   }
 }
 
