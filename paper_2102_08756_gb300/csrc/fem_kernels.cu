@@ -56,7 +56,9 @@ __device__ __forceinline__ void load_window(const R* __restrict__ xl, long long 
 // F += (-K) x from the element layer on one side of the node: side 0 (below)
 // spans node layers l-1 (lo) and l (hi), side 1 (above) layers l and l+1.  Fully
 // unrolled: every stencil index is a compile-time constant, and the stencil holds
-// -K so that each entry is one fused multiply-add.
+// -K so that each entry is one fused multiply-add.  The entries that vanish by
+// symmetry (stencil_entry_vanishes) are skipped: 236 multiply-adds per node
+// instead of 324.
 template <int SIDE, class R>
 __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>& lo,
                                            const Window<R>& hi, R (&F)[3]) {
@@ -69,11 +71,11 @@ __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>&
       for (int ox = 0; ox < 3; ++ox) {
         const int s = SIDE * 18 * 9 + ((ox * 2 + oy) * 3 + oz) * 9;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          F[c] = fma(S.s[s + 3 * c], w.v[0][oz][ox], F[c]);
-          F[c] = fma(S.s[s + 3 * c + 1], w.v[1][oz][ox], F[c]);
-          F[c] = fma(S.s[s + 3 * c + 2], w.v[2][oz][ox], F[c]);
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            if (!stencil_entry_vanishes(ox, oz, c, d))
+              F[c] = fma(S.s[s + 3 * c + d], w.v[d][oz][ox], F[c]);
       }
   }
 }

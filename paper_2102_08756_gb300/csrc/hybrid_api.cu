@@ -133,6 +133,16 @@ void build_stencil(const double K[24][24], double* out) {
             }
       }
   }
+  // the entries that vanish by the mirror symmetry of the elements (they hold
+  // only the rounding of terms that cancel) become exact zeros
+  for (int side = 0; side < 2; ++side)
+    for (int ox = 0; ox < 3; ++ox)
+      for (int oy = 0; oy < 2; ++oy)
+        for (int oz = 0; oz < 3; ++oz)
+          for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d)
+              if (sbim::fem::stencil_entry_vanishes(ox, oz, c, d))
+                out[side * 162 + ((ox * 2 + oy) * 3 + oz) * 9 + 3 * c + d] = 0.0;
 }
 
 sbim::fem::MeshArgs mesh_args(const sbim_hybrid_ctx* c) {
