@@ -243,6 +243,17 @@ int sbim_set_window(sbim_handle h, double window);
 int sbim_check_device(sbim_handle h);
 
 /*
+ * sbim_selftest_wait_timeout -- exercises the failure path of the bounded
+ * device waits without any fault: one CTA waits, with the convolution's
+ * bounded mbarrier wait, on a barrier that nothing ever completes; after the
+ * wait's wall-time limit (1 s) it gives up and sets the handle's device error
+ * word.  Returns SBIM_OK when sbim_check_device then reports SBIM_ERR_TIMEOUT
+ * and the word is clear again (the handle stays usable), SBIM_ERR_STATE if the
+ * failure went unreported.  Synchronises the handle's stream; takes ~1 s.
+ */
+int sbim_selftest_wait_timeout(sbim_handle h);
+
+/*
  * sbim_spectral_response_noalloc -- the non-local traction spectrum of one
  * half-space for a caller-supplied displacement-spectrum history, without
  * allocating any device memory.  The paper has no counterpart: this entry point

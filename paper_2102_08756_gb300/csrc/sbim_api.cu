@@ -699,6 +699,19 @@ int sbim_check_device(sbim_handle h) {
   return SBIM_OK;
 }
 
+int sbim_selftest_wait_timeout(sbim_handle h) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  int rc = sbim_check_device(h);                 // start from a clear error word
+  if (rc != SBIM_OK) return rc;
+  CU(sbim::launch_wait_selftest(h->d_err, h->stream));
+  rc = sbim_check_device(h);                     // waits for the stream
+  if (rc == SBIM_ERR_TIMEOUT) {
+    g_err.clear();
+    return sbim_check_device(h);                 // and the word is clear again
+  }
+  return fail(SBIM_ERR_STATE, "the bounded wait did not report its failure (status %d)", rc);
+}
+
 int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
   if (variant < 0 || variant > 3) return fail(SBIM_ERR_ARG, "variant must be 0..3");

@@ -2,9 +2,32 @@
 // pipeline shape (the instantiations live in one translation unit per
 // precision so that they compile in parallel).
 #include "../../include/sbim.h"
+#include "sbim_conv_tma.cuh"
 #include "sbim_internal.cuh"
 
 namespace sbim {
+
+namespace {
+// The failure path of the bounded waits, exercised on purpose: the CTA waits on
+// an mbarrier that expects one arrival and gets none (no copy is ever issued to
+// it), with the same bounded wait the convolution uses.  The wait gives up after
+// its wall-time limit and the CTA records the failure in the error word.
+__global__ void wait_selftest_kernel(int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(tma::smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool landed = tma::mbar_wait(tma::smem_addr(&bar), 0u, err);
+  if (!__syncthreads_and(landed) && threadIdx.x == 0) atomicExch(err, 1);
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_conv_tma_f32(const StepArgs& a, int kahan, int shape, cudaStream_t st,
                                  const BatchLaunch* batch, bool prep);

@@ -79,6 +79,8 @@ int conv_tma_ctas_per_sm(int precision, int shape);
 // Set the shared-memory attributes of a shape's kernels (done before any launch,
 // so that launches can be captured in a CUDA graph).
 cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
+// One CTA whose bounded mbarrier wait can never complete (sbim_selftest_wait_timeout).
+cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_rewind(long long* step, cudaStream_t st);
 cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st);

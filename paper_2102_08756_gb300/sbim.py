@@ -54,6 +54,7 @@ def lib():
     L.sbim_set_conv_config.argtypes = [vp, i, i]
     L.sbim_set_window.argtypes = [vp, d]
     L.sbim_check_device.argtypes = [vp]
+    L.sbim_selftest_wait_timeout.argtypes = [vp]
     L.sbim_spectral_response_noalloc.argtypes = [i, i, d, d, d, d, d, d, i, i, vp, vp, vp]
     L.sbim_destroy.argtypes = [vp]
     L.sbim_fault_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, i, i, i, vp]
@@ -201,6 +202,10 @@ def sbim_set_window(h, window):
 
 def sbim_check_device(h):
     _check(lib().sbim_check_device(h))
+
+
+def sbim_selftest_wait_timeout(h):
+    _check(lib().sbim_selftest_wait_timeout(h))
 
 
 def sbim_spectral_response_noalloc(n1, n3, L1, L3, cs, cp, rho, dt, side, n_lags, uhat_ptr,
