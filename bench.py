@@ -266,6 +266,21 @@ def time_oracle(sample, min_seconds=0.0):
     return sample["n"] * sample["L"] * MACS_PER_PAIR * reps / el, el, reps
 
 
+def host_cpu():
+    """The host the oracle baseline ran on: CPU model and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -287,7 +302,7 @@ def run_reference(args):
         "config": {"workload": workload_name(c, "fp64", 0) + " (FP64 CPU oracle, sampled modes)",
                    "n1": c["n1"], "n3": c["n3"], "n_cut": c["n_cut"]},
         "cpu_baseline": {"value": value, "unit": "MAC/s", "cores": 1, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "host": host_cpu()},
         "e2e": {"value": value, "unit": "MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -434,7 +449,8 @@ def run_native(args):
         rate, secs, reps = time_oracle(smp, min_seconds=10.0)
         cpu = {"value": rate, "unit": "MAC/s", "cores": 1, "kind": "oracle",
                "sample": (f"{smp['n']} random modes x {smp['L']} lags of the full-history "
-                          f"per-mode operator, repeated {reps}x ({secs:.1f} s, one thread)")}
+                          f"per-mode operator, repeated {reps}x ({secs:.1f} s, one thread)"),
+               "host": host_cpu()}
     line = {
         "metric": "SBIM mode-history MACs/s", "value": value, "unit": "MAC/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms_step,
