@@ -326,10 +326,12 @@ int sbim_batch_capture(sbim_batch b, const void* const* u, const void* const* v,
 int sbim_batch_replay(sbim_batch b);
 
 /*
- * sbim_batch_set_conv_config -- launch of the batch's persistent convolution:
- * TMA pipeline shape (1..3, as in sbim_set_conv_config) and lags per work item
- * (0: 256).  Results do not depend on it beyond float rounding.  Drops a
- * captured graph: capture again before replaying.
+ * sbim_batch_set_conv_config -- launch of the batch's convolution: TMA pipeline
+ * shape 1..3 (as in sbim_set_conv_config) on persistent CTAs that take work
+ * items from a counter, or 4..6 (shapes 1..3) with one CTA per work item; and
+ * lags per work item (0: 1024).  The results are the same for every launch
+ * with the same lags per item (each item writes its own partial sums).  Drops
+ * a captured graph: capture again before replaying.
  */
 int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
 

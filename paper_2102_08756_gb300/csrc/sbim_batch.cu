@@ -15,6 +15,7 @@
 
 struct sbim_batch_ctx {
   int nb = 0, prec = SBIM_FP32, kahan = 1, shape = 2;
+  bool per_item = false;    // one CTA per work item instead of persistent CTAs
   bool owns = true;
   cudaStream_t stream = nullptr;
   std::vector<sbim_handle> h;
@@ -181,6 +182,7 @@ int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void*
   bl.nb = b->nb;
   bl.counter = b->d_counter;
   bl.ctas = b->ctas;
+  bl.items = b->per_item ? b->total_items : 0;
   const sbim::StepArgs a0 = sbim::handle_step_args(b->h[0]);
   BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl));
   BCU(sbim::launch_assemble_batch(bl, b->total_tiles, b->prec, b->kahan, b->stream));
@@ -300,10 +302,11 @@ int sbim_batch_replay(sbim_batch b) {
 
 int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
   if (!b) return bfail(SBIM_ERR_ARG, "NULL batch");
-  if (shape < 1 || shape > 3) return bfail(SBIM_ERR_ARG, "shape must be 1..3");
+  if (shape < 1 || shape > 6) return bfail(SBIM_ERR_ARG, "shape must be 1..6");
   if (lags_per_item < 0) return bfail(SBIM_ERR_ARG, "lags_per_item must be >= 0");
   drop_graph(b);
-  return configure(b, shape, lags_per_item ? lags_per_item : kBatchLags);
+  b->per_item = shape > 3;
+  return configure(b, shape > 3 ? shape - 3 : shape, lags_per_item ? lags_per_item : kBatchLags);
 }
 
 int sbim_batch_member(sbim_batch b, int i, sbim_handle* h) {

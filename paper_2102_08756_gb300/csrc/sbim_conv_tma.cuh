@@ -393,9 +393,36 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
   }
 }
 
+// One CTA per (update, tile, chunk) item of a batch (the hardware block
+// scheduler hands the items out; no work counter, and no barrier phases carried
+// from item to item, so its register needs are those of the single-update
+// kernel).  Same item order as the persistent kernel.
+template <class S, int KAHAN, int NS, int KS, int MINB>
+__global__ void __launch_bounds__(kOrbitTile, MINB)
+conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
+                      int nb) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[NS];
+  __shared__ int s_tile, s_chunk;
+  __shared__ StepArgs s_args;
+  if (threadIdx.x == 0) {
+    const int it = blockIdx.x;
+    int s = 0;
+    while (s + 1 < nb && item_prefix[s + 1] <= it) ++s;
+    s_args = args[s];
+    const int tiles = s_args.n_orb_pad / kOrbitTile;
+    const int local = it - item_prefix[s];
+    s_tile = local % tiles;
+    s_chunk = local / tiles;
+  }
+  init_barriers<NS>(full);   // its __syncthreads publishes the item too
+  unsigned gstage = 0;
+  conv_tma_item<S, KAHAN, NS, KS>(s_args, s_tile, s_chunk, smem, full, gstage);
+}
+
 // Launch one instantiation (sets the dynamic shared-memory attribute once).
-// With `batch` set, launches the persistent kernel over the batch's items on
-// `batch->ctas` CTAs instead.
+// With `batch` set, launches over the batch's items instead: one CTA per item
+// when `batch->items` > 0, else the persistent kernel on `batch->ctas` CTAs.
 template <class S, int KAHAN, int NS, int KS, int MINB>
 cudaError_t prepare_shape() {
   static bool attr_set = false;
@@ -405,6 +432,9 @@ cudaError_t prepare_shape() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv_tma_items_kernel<S, KAHAN, NS, KS, MINB>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -419,7 +449,10 @@ cudaError_t launch_shape(const StepArgs& a, cudaStream_t st, const BatchLaunch* 
   constexpr int bytes = smem_bytes<S, NS, KS>();
   const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB>();
   if (pe != cudaSuccess || prepare_only) return pe;
-  if (batch) {
+  if (batch && batch->items > 0) {
+    conv_tma_items_kernel<S, KAHAN, NS, KS, MINB><<<batch->items, kOrbitTile, bytes, st>>>(
+        batch->args, batch->item_prefix, batch->nb);
+  } else if (batch) {
     conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB><<<batch->ctas, kOrbitTile, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb, batch->counter);
   } else {

@@ -64,6 +64,7 @@ struct BatchLaunch {
   int nb;
   int* counter;             // work counter, zero before each launch
   int ctas;                 // persistent CTAs
+  int items;                // > 0: one CTA per item (this many), no persistent CTAs
 };
 
 cudaError_t launch_conv(const StepArgs& a, int precision, int kahan, cudaStream_t s);

@@ -63,10 +63,11 @@ def autotune(h, u, v, steps=6, chunkings=None, cache=None, verbose=False):
     return best, table
 
 
-def autotune_hybrid_batch(b, stream, shapes=(1, 2, 3), lags=(128, 256, 512, 1024), steps=4):
-    """Time whole captured ensemble steps of a hybrid batch for every (pipeline
-    shape, lags per work item) of the persistent convolution and keep the
-    fastest (the batch is left captured with it).  Each trial advances the
+def autotune_hybrid_batch(b, stream, shapes=(1, 2, 3, 4, 5, 6), lags=(256, 512, 1024, 2048),
+                          steps=4):
+    """Time whole captured ensemble steps of a hybrid batch for every (launch
+    shape: 1-3 persistent, 4-6 one CTA per item; lags per work item) of the
+    batched convolution and keep the fastest (the batch is left captured with it).  Each trial advances the
     ensemble by ``steps + 1`` steps."""
     from . import sbim as B
     table = []

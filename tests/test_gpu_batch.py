@@ -43,10 +43,10 @@ def _fields(hist, m):
     return u, v
 
 
-@pytest.mark.parametrize("shape,lags", [(None, None), (3, 256), (2, 64)])
+@pytest.mark.parametrize("shape,lags", [(None, None), (3, 256), (2, 64), (5, 64), (4, 1024)])
 def test_batch_equals_members_stepped_alone(shape, lags):
-    """Default launch (pipeline shape 1, 1024-lag items) and two others set with
-    sbim_batch_set_conv_config."""
+    """Default launch (pipeline shape 1, 1024-lag items) and others set with
+    sbim_batch_set_conv_config, persistent (1-3) and one CTA per item (4-6)."""
     from paper_2102_08756_gb300.sbim import SBIM
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -57,7 +57,10 @@ def test_batch_equals_members_stepped_alone(shape, lags):
         for (a, c, n_cut, side) in MEMBERS:
             h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "fp32", True,
                      stream=stream)
-            h.set_conv_config(1, 1024) if shape is None else h.set_conv_config(shape, lags)
+            if shape is None:
+                h.set_conv_config(1, 1024)
+            else:
+                h.set_conv_config(shape - 3 if shape > 3 else shape, lags)
             alone.append(h)
         oracles = [SBIMOracle(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side)
                    for (a, c, n_cut, side) in MEMBERS[:2]]
@@ -111,7 +114,7 @@ def test_graph_replay_equals_direct_steps():
         B.sbim_batch_destroy(b2)
 
 
-@pytest.mark.parametrize("shape,lags", [(None, None), (3, 16)])
+@pytest.mark.parametrize("shape,lags", [(None, None), (3, 16), (5, 16)])
 def test_hybrid_ensemble_batch_and_graph(shape, lags):
     """Three coupled scenarios with different grids, slab thicknesses, fault laws
     and cutoffs: the ensemble step (one batched SBIM launch for the six
@@ -137,8 +140,9 @@ def test_hybrid_ensemble_batch_and_graph(shape, lags):
         alone, batched, graphed = make(), make(), make()
         for x in alone:
             _, _, top, bot = B.sbim_hybrid_info(x.h)
-            B.sbim_set_conv_config(top, shape or 1, lags or 1024)
-            B.sbim_set_conv_config(bot, shape or 1, lags or 1024)
+            single = 1 if shape is None else (shape - 3 if shape > 3 else shape)
+            B.sbim_set_conv_config(top, single, lags or 1024)
+            B.sbim_set_conv_config(bot, single, lags or 1024)
         b1 = B.sbim_hybrid_batch_create([x.h for x in batched])
         b2 = B.sbim_hybrid_batch_create([x.h for x in graphed])
         if shape is not None:
