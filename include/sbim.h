@@ -329,7 +329,8 @@ int sbim_batch_replay(sbim_batch b);
  * sbim_batch_set_conv_config -- launch of the batch's convolution: TMA pipeline
  * shape 1..3 (as in sbim_set_conv_config) on persistent CTAs that take work
  * items from a counter, or 4..6 (shapes 1..3) with one CTA per work item; and
- * lags per work item (0: 1024).  The results are the same for every launch
+ * lags per work item (0: 1024).  Default: one CTA per 1024-lag item with shape
+ * 2 for float history, persistent shape 1 for bf16.  The results are the same for every launch
  * with the same lags per item (each item writes its own partial sums).  Drops
  * a captured graph: capture again before replaying.
  */

@@ -68,12 +68,16 @@ void brelease(sbim_batch_ctx* b) {
   delete b;
 }
 
-// Default launch of the persistent kernel: work items of up to 1024 lags of one
-// orbit tile, and pipeline shape 1 (4 stages x 2 lags, 2 CTAs/SM; 8 x 2 for bf16
-// hi-only), the fastest of the shapes and item sizes the batch autotuner timed on
-// GB300 for a 32-scenario coupled ensemble (25.2 ms per step, against 26.0 ms
-// for shape 3 with 256-lag items).  sbim_batch_set_conv_config changes both.
+// Default launch: one CTA per work item of up to 1024 lags of one orbit tile,
+// with the single-update kernel's pipeline shape for float history (shape 2:
+// 3 stages x 2 lags, 3 CTAs/SM) and persistent CTAs with shape 1 for bf16.  On
+// GB300, for a 32-scenario coupled ensemble, the batch autotuner timed 23.67 ms
+// per step for this launch against 23.86 ms for the best persistent one (shape 1,
+// 1024-lag items) and 24.03-26.74 ms for the other persistent shapes.
+// sbim_batch_set_conv_config changes both.
 constexpr int kBatchLags = 1024;
+constexpr int kBatchShapeF32 = 2;
+constexpr int kBatchShapeBF16 = 1;
 constexpr int kSideStreams = 8;
 
 int fork(sbim_batch_ctx* b) {
@@ -91,8 +95,6 @@ int join(sbim_batch_ctx* b) {
 }
 
 cudaStream_t side_of(sbim_batch_ctx* b, int i) { return b->side[i % b->side.size()]; }
-constexpr int kBatchShapeF32 = 1;
-constexpr int kBatchShapeBF16 = 1;
 
 void drop_graph(sbim_batch_ctx* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -154,6 +156,7 @@ int setup(sbim_batch_ctx* b) {
     if (prec == SBIM_FP64) return bfail(SBIM_ERR_ARG, "batches use float or bf16 history");
   }
   b->prec = prec0; b->kahan = kahan0; b->stream = (cudaStream_t)st0;
+  b->per_item = prec0 == SBIM_FP32;
   const int k = b->nb < kSideStreams ? b->nb : kSideStreams;
   BCU(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
   for (int i = 0; i < k; ++i) {

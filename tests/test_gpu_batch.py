@@ -45,7 +45,7 @@ def _fields(hist, m):
 
 @pytest.mark.parametrize("shape,lags", [(None, None), (3, 256), (2, 64), (5, 64), (4, 1024)])
 def test_batch_equals_members_stepped_alone(shape, lags):
-    """Default launch (pipeline shape 1, 1024-lag items) and others set with
+    """Default launch (one CTA per 1024-lag item, pipeline shape 2) and others set with
     sbim_batch_set_conv_config, persistent (1-3) and one CTA per item (4-6)."""
     from paper_2102_08756_gb300.sbim import SBIM
     stream = torch.cuda.Stream()
@@ -58,7 +58,7 @@ def test_batch_equals_members_stepped_alone(shape, lags):
             h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "fp32", True,
                      stream=stream)
             if shape is None:
-                h.set_conv_config(1, 1024)
+                h.set_conv_config(2, 1024)
             else:
                 h.set_conv_config(shape - 3 if shape > 3 else shape, lags)
             alone.append(h)
@@ -140,7 +140,7 @@ def test_hybrid_ensemble_batch_and_graph(shape, lags):
         alone, batched, graphed = make(), make(), make()
         for x in alone:
             _, _, top, bot = B.sbim_hybrid_info(x.h)
-            single = 1 if shape is None else (shape - 3 if shape > 3 else shape)
+            single = 2 if shape is None else (shape - 3 if shape > 3 else shape)
             B.sbim_set_conv_config(top, single, lags or 1024)
             B.sbim_set_conv_config(bot, single, lags or 1024)
         b1 = B.sbim_hybrid_batch_create([x.h for x in batched])
