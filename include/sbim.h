@@ -130,7 +130,8 @@ int sbim_step_adjoint(sbim_handle h, const void* tau_bar, void* u_bar, void* v_b
  */
 int sbim_set_far_field(sbim_handle h, const double tau_inf[3]);
 
-/* sbim_reset -- forget the history; the next sbim_step is step 0 again. */
+/* sbim_reset -- forget the history; the next sbim_step is step 0 again, from the
+ * equilibrium start of Section 2.1 (earlier displacements zero in Eq. (SBI)). */
 int sbim_reset(sbim_handle h);
 
 /*
@@ -151,11 +152,13 @@ int sbim_step_repeat(sbim_handle h, const void* u, const void* v, void* tau);
  * counter goes back by one and the next call evaluates the same time level again,
  * overwriting that level's history entry.  This is what a predictor-corrector
  * time stepper needs (evaluate at a predicted displacement, rewind, evaluate at the
- * corrected one).  Stream-ordered; SBIM_ERR_STATE at step 0.
+ * corrected one), as the SBIM-only fault solver of Section 3's comparison does.
+ * Stream-ordered; SBIM_ERR_STATE at step 0.
  */
 int sbim_rewind(sbim_handle h);
 
-/* sbim_get_step -- number of sbim_step calls since creation or the last reset. */
+/* sbim_get_step -- number of sbim_step calls since creation or the last reset (the time
+ * level n of Eq. (SBI)). */
 int sbim_get_step(sbim_handle h, long long* n);
 
 /*
@@ -190,6 +193,7 @@ int sbim_load(sbim_handle h, const void* buf, size_t bytes);
  *               (Nyquist bins count twice or four times, padding included)
  *   hist_bytes  bytes of the history ring buffer
  *   table_nodes entries of the interpolated kernel table
+ * Library utility: the paper has no counterpart.
  */
 int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
                   long long* hist_bytes, long long* table_nodes);
@@ -200,7 +204,8 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
  * around its stages; sbim_stage_times waits for them and returns the summed
  * milliseconds of (0) forward FFT, (1) history convolution, (2) reduction and
  * assembly, (3) inverse FFT, (4) traction epilogue, and the number of steps
- * summed.  Enabling clears the sums.
+ * summed (the stages of the spectral evaluation of Eq. (SBI), Section 2.3).
+ * Enabling clears the sums.
  */
 int sbim_set_profiling(sbim_handle h, int enable);
 int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
@@ -224,7 +229,7 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
 int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta);
 
 /*
- * sbim_set_window -- mode-dependent truncation of the convolution (the paper cites
+ * sbim_set_window -- mode-dependent truncation of the convolution (Section 1 cites
  * the truncation of Lapusta et al. without giving a rule): a window fixed in the
  * dimensionless time T = |k| c_s t, so mode k keeps its lags m with
  * m |k| c_s dt <= window (at most n_cut; k = 0 keeps n_cut).  Long-wavelength modes
@@ -238,7 +243,8 @@ int sbim_set_window(sbim_handle h, double window);
  * sbim_check_device -- wait for the handle's stream and report whether any
  * bounded device-side wait of the convolution gave up since the last check
  * (SBIM_ERR_TIMEOUT; the tractions computed since then are invalid).  Clears the
- * flag.  sbim_step_host performs this check after every step.
+ * flag.  sbim_step_host performs this check after every step.  Library utility: the
+ * paper has no counterpart.
  */
 int sbim_check_device(sbim_handle h);
 
@@ -249,7 +255,8 @@ int sbim_check_device(sbim_handle h);
  * wait's wall-time limit (1 s) it gives up and sets the handle's device error
  * word.  Returns SBIM_OK when sbim_check_device then reports SBIM_ERR_TIMEOUT
  * and the word is clear again (the handle stays usable), SBIM_ERR_STATE if the
- * failure went unreported.  Synchronises the handle's stream; takes ~1 s.
+ * failure went unreported.  Synchronises the handle's stream; takes ~1 s.  Library
+ * utility: the paper has no counterpart.
  */
 int sbim_selftest_wait_timeout(sbim_handle h);
 
@@ -311,8 +318,9 @@ int sbim_batch_create(sbim_batch* out, int nb, const int* n1, const int* n3, con
                       const double* dt, const int* n_cut, const int* side, int precision,
                       int kahan, void* stream);
 
-/* sbim_batch_step -- one update of every member: u, v, tau are HOST arrays of nb
- * DEVICE pointers ([3][n3[i]][n1[i]] each), as for sbim_step.  Stream-ordered. */
+/* sbim_batch_step -- one update of every member (Eq. (SBI) each): u, v, tau are HOST
+ * arrays of nb DEVICE pointers ([3][n3[i]][n1[i]] each), as for sbim_step.
+ * Stream-ordered. */
 int sbim_batch_step(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
 
 /*
@@ -320,7 +328,8 @@ int sbim_batch_step(sbim_batch b, const void* const* u, const void* const* v, vo
  * (fixed) buffers into a CUDA graph on the batch's stream (which must not be the
  * legacy default stream), then replay it: each replay is one step of every
  * member, reading whatever the buffers hold at that point of the stream.  The
- * capture itself enqueues no work.  Re-capturing replaces the graph.
+ * capture itself enqueues no work.  Re-capturing replaces the graph.  Library
+ * utility: the paper has no counterpart.
  */
 int sbim_batch_capture(sbim_batch b, const void* const* u, const void* const* v, void* const* tau);
 int sbim_batch_replay(sbim_batch b);
@@ -330,13 +339,16 @@ int sbim_batch_replay(sbim_batch b);
  * shape 1..3 (as in sbim_set_conv_config) on persistent CTAs that take work
  * items from a counter, or 4..6 (shapes 1..3) with one CTA per work item; and
  * lags per work item (0: 1024).  Default: one CTA per 1024-lag item with shape
- * 2 for float history, persistent shape 1 for bf16.  The results are the same for every launch
- * with the same lags per item (each item writes its own partial sums).  Drops
- * a captured graph: capture again before replaying.
+ * 2 for float history, persistent shape 1 for bf16.  The results are the same
+ * for every launch with the same lags per item (each item writes its own
+ * partial sums).  Drops a captured graph: capture again before replaying.
+ * Library utility (the launch of the Section 2.3 convolution): the paper has no
+ * counterpart.
  */
 int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
 
-/* sbim_batch_member -- the handle of member i (owned by the batch). */
+/* sbim_batch_member -- the handle of member i (owned by the batch).  Library utility:
+ * the paper has no counterpart. */
 int sbim_batch_member(sbim_batch b, int i, sbim_handle* h);
 
 int sbim_batch_destroy(sbim_batch b);
@@ -376,25 +388,30 @@ int sbim_fault_create(sbim_fault* out, int n1, int n3, double L1, double L3, dou
                       double cp, double rho, double dt, int n_cut, int precision, int symmetric,
                       void* stream);
 
-/* sbim_fault_set_fault -- as sbim_hybrid_set_fault: HOST maps [n3][n1] of mu_s and
- * the x1 shear prestress tau0 (Pa); mu_k, Dc (m), sigma0 (compression positive, Pa). */
+/* sbim_fault_set_fault -- the linear slip-weakening law of Section 2.1 (Eq. (slipweak)),
+ * as sbim_hybrid_set_fault: HOST maps [n3][n1] of mu_s and the x1 shear prestress tau0
+ * (Pa); mu_k, Dc (m), sigma0 (compression positive, Pa). */
 int sbim_fault_set_fault(sbim_fault h, const double* mu_s, const double* tau0, double mu_k,
                          double Dc, double sigma0);
 
 /* sbim_fault_set_state / get_state -- device [2][3][n3][n1] displacement and
- * velocity of the two faces (NULL: zero on set, skip on get).  The symmetric
- * solver replaces the lower face by the mirror image of the upper one. */
+ * velocity of the two faces (NULL: zero on set, skip on get), the solver's whole
+ * state besides the half-spaces' histories.  The symmetric solver replaces the lower
+ * face by the mirror image of the upper one (Section 3's symmetry plane). */
 int sbim_fault_set_state(sbim_fault h, const void* u, const void* v);
 int sbim_fault_get_state(sbim_fault h, void* u, void* v);
 
-/* sbim_fault_step -- one time step, stream-ordered, no host sync. */
+/* sbim_fault_step -- one time step of the solver described at sbim_fault_create
+ * (Sections 2.1 and 2.3), stream-ordered, no host sync. */
 int sbim_fault_step(sbim_fault h);
 
 /* sbim_fault_fields -- device outputs [3][n3][n1] (any may be NULL): slip u+ - u-,
- * slip rate v+ - v- and fault traction perturbation of the last step (Pa). */
+ * slip rate v+ - v- and fault traction perturbation of the last step (Pa), the fault
+ * quantities of Section 2.1. */
 int sbim_fault_fields(sbim_fault h, void* slip, void* slip_rate, void* traction);
 
-/* sbim_fault_info -- steps taken and the SBIM handles (lower is NULL when symmetric). */
+/* sbim_fault_info -- steps taken and the SBIM handles (lower is NULL when symmetric).
+ * Library utility: the paper has no counterpart. */
 int sbim_fault_info(sbim_fault h, long long* steps, sbim_handle* upper, sbim_handle* lower);
 
 int sbim_fault_destroy(sbim_fault h);
@@ -438,7 +455,8 @@ int sbim_hybrid_set_fault(sbim_hybrid h, const double* mu_s, const double* tau0,
                           double Dc, double sigma0);
 
 /* sbim_hybrid_set_state / get_state -- device pointers [L][3][n3][n1] of the handle's
- * element type for u, v, a (NULL: zero on set, skip on get).  Stream-ordered. */
+ * element type for u, v, a (NULL: zero on set, skip on get), the FE state of the time
+ * stepping of Section 2.2.  Stream-ordered. */
 int sbim_hybrid_set_state(sbim_hybrid h, const void* u, const void* v, const void* a);
 int sbim_hybrid_get_state(sbim_hybrid h, void* u, void* v, void* a);
 
@@ -451,7 +469,7 @@ int sbim_hybrid_step(sbim_hybrid h, const void* force);
 
 /* sbim_hybrid_fault_fields -- device outputs [3][n3][n1] (any may be NULL): slip
  * vector u+ - u-, slip rate v+ - v-, and the fault traction perturbation of the
- * last step (Pa). */
+ * last step (Pa): the fault quantities of Section 2.1. */
 int sbim_hybrid_fault_fields(sbim_hybrid h, void* slip, void* slip_rate, void* traction);
 
 /*
@@ -485,7 +503,8 @@ int sbim_hybrid_adjoint_step(sbim_hybrid h, const void* u, const void* v, const 
                              void* lu, void* lv, void* la, void* dc_bar);
 
 /* sbim_hybrid_info -- node layers, steps taken, and the two SBIM handles (NULL
- * with free surfaces), e.g. for profiling or sbim_set_conv_config. */
+ * with free surfaces), e.g. for profiling or sbim_set_conv_config.  Library utility:
+ * the paper has no counterpart. */
 int sbim_hybrid_info(sbim_hybrid h, int* layers, long long* steps, sbim_handle* top,
                      sbim_handle* bottom);
 
@@ -496,9 +515,11 @@ int sbim_hybrid_destroy(sbim_hybrid h);
  * fault laws, cutoffs): sbim_hybrid_batch_create groups existing hybrid handles
  * (SBIM boundaries, SBIM_FP32, one shared stream; not owned by the batch).  A
  * batch step runs every member's FE stages and ONE batched SBIM step over all
- * 2 nb half-spaces (sbim_batch: one persistent convolution launch).  capture /
- * replay put one batch step in a CUDA graph on the shared (non-default) stream.
- * Destroy the batch before its members.
+ * 2 nb half-spaces (sbim_batch: one batched convolution launch); the members' FE
+ * stages run concurrently on side streams.  capture / replay put one batch step in a
+ * CUDA graph on the shared (non-default) stream.  Destroy the batch before its
+ * members.  Each member steps as in Section 2.4; the batching is a library utility
+ * with no counterpart in the paper.
  */
 typedef struct sbim_hybrid_batch_ctx* sbim_hybrid_batch;
 int sbim_hybrid_batch_create(sbim_hybrid_batch* out, int nb, const sbim_hybrid* members);
@@ -506,14 +527,17 @@ int sbim_hybrid_batch_step(sbim_hybrid_batch b);
 int sbim_hybrid_batch_capture(sbim_hybrid_batch b);
 int sbim_hybrid_batch_replay(sbim_hybrid_batch b);
 /* sbim_hybrid_batch_set_conv_config -- as sbim_batch_set_conv_config for the
- * batch's 2 nb half-spaces; drops a captured graph. */
+ * batch's 2 nb half-spaces; drops a captured graph.  Library utility: the paper has
+ * no counterpart. */
 int sbim_hybrid_batch_set_conv_config(sbim_hybrid_batch b, int shape, int lags_per_item);
 int sbim_hybrid_batch_destroy(sbim_hybrid_batch b);
 
-/* sbim_destroy -- free everything the handle owns; NULL is accepted. */
+/* sbim_destroy -- free everything the handle owns; NULL is accepted.  Library utility:
+ * the paper has no counterpart. */
 int sbim_destroy(sbim_handle h);
 
-/* sbim_last_error -- message of the calling thread's last failure ("" if none). */
+/* sbim_last_error -- message of the calling thread's last failure ("" if none).  Library
+ * utility: the paper has no counterpart. */
 const char* sbim_last_error(void);
 
 #ifdef __cplusplus
