@@ -169,3 +169,52 @@ def test_hybrid_ensemble_batch_and_graph(shape, lags):
         B.sbim_hybrid_batch_destroy(b2)
         for x in alone + batched + graphed:
             x.close()
+
+
+def test_ensemble_members_at_full_size_equal_members_alone():
+    """The ensemble configuration's own scenarios at their full sizes (the first
+    four of the seeded draw the benchmark uses), in the benchmark's launch: the
+    hybrid batch and its graph replay equal the scenarios stepped alone with the
+    same lag chunking, bit for bit, over the first 25 steps of the rupture."""
+    import bench
+    from paper_2102_08756_gb300 import sbim as B
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    scen = bench.ensemble_draw()[:4]
+    h = 100.0
+    dt = 0.3 * h / CP
+    stream = torch.cuda.Stream()
+
+    def make():
+        out = []
+        for sc in scen:
+            n = sc["n"]
+            x = Hybrid(n, sc["n2"], n, h, CS, CP, RHO, dt, sc["n_cut"], "fp32", True, True,
+                       stream=stream)
+            c = (np.arange(n) - n / 2 + 0.5) * h
+            X3, X1 = np.meshgrid(c, c, indexing="ij")
+            patch = (np.abs(X1) <= 1.5e3) & (np.abs(X3) <= 1.5e3)
+            x.set_fault(0.677, np.where(patch, 1.005 * 0.677 * 120e6, sc["ratio"] * 0.677 * 120e6),
+                        0.525, sc["Dc"], 120e6)
+            out.append(x)
+        return out
+
+    with torch.cuda.stream(stream):
+        alone, graphed = make(), make()
+        for x in alone:
+            _, _, top, bot = B.sbim_hybrid_info(x.h)
+            B.sbim_set_conv_config(top, 2, 1024)
+            B.sbim_set_conv_config(bot, 2, 1024)
+        b = B.sbim_hybrid_batch_create([x.h for x in graphed])
+        B.sbim_hybrid_batch_capture(b)
+        for _ in range(25):
+            for x in alone:
+                x.step()
+            B.sbim_hybrid_batch_replay(b)
+        stream.synchronize()
+        for a, g in zip(alone, graphed):
+            assert torch.equal(a.fault_fields()[1], g.fault_fields()[1])
+            assert torch.equal(a.get_state()[0], g.get_state()[0])
+        assert max(float(x.fault_fields()[1].abs().max()) for x in alone) > 0.1
+        B.sbim_hybrid_batch_destroy(b)
+        for x in alone + graphed:
+            x.close()
