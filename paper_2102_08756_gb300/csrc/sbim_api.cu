@@ -152,9 +152,30 @@ struct sbim_ctx {
 
 namespace {
 
+// Integer weights (a, b) with L1 / L3 = a / b exactly, a and b coprime and
+// small, so that |k|^2 (L1 L3 / 2 pi)^2 = (j1 b)^2 + (j3 a)^2 is an exact integer
+// key; {0, 0} when the period ratio is not such a fraction (or the key could
+// overflow), and bins are then grouped by their floating-point |k|^2.
+void period_ratio(const sbim_ctx& c, long long& a, long long& b) {
+  a = b = 0;
+  for (long long bb = 1; bb <= 4096; ++bb) {
+    const double aa = std::nearbyint(c.L1 * (double)bb / c.L3);
+    if (aa < 1.0 || aa > 4096.0 || c.L1 * (double)bb != c.L3 * aa) continue;
+    const double big = std::pow((double)(c.n1 / 2) * (double)bb, 2) +
+                       std::pow((double)(c.n3 / 2) * aa, 2);
+    if (big < 4e18) {
+      a = (long long)aa;
+      b = bb;
+    }
+    return;
+  }
+}
+
 // Group the half-spectrum bins into |k|-sorted orbits of <= 4 members.
 void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_orb) {
-  const bool square = (c.n1 == c.n3) && (c.L1 == c.L3);
+  long long ra, rb;
+  period_ratio(c, ra, rb);
+  const bool exact = ra > 0;
   struct Rec {
     long long ikey;
     double dkey;
@@ -169,14 +190,14 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
       r.j1 = j1;
       r.r3 = r3;
       r.j3 = j3;
-      r.ikey = square ? (long long)j1 * j1 + (long long)j3 * j3 : 0;
+      r.ikey = exact ? (j1 * rb) * (j1 * rb) + (j3 * ra) * (j3 * ra) : 0;
       const double a = j1 / c.L1, b = j3 / c.L3;
       r.dkey = a * a + b * b;
       recs.push_back(r);
     }
   }
-  auto less = [square](const Rec& x, const Rec& y) {
-    if (square) {
+  auto less = [exact](const Rec& x, const Rec& y) {
+    if (exact) {
       if (x.ikey != y.ikey) return x.ikey < y.ikey;
     } else if (x.dkey != y.dkey) {
       return x.dkey < y.dkey;
@@ -185,8 +206,8 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
     return x.r3 < y.r3;
   };
   std::sort(recs.begin(), recs.end(), less);
-  auto same = [square](const Rec& x, const Rec& y) {
-    return square ? x.ikey == y.ikey : x.dkey == y.dkey;
+  auto same = [exact](const Rec& x, const Rec& y) {
+    return exact ? x.ikey == y.ikey : x.dkey == y.dkey;
   };
 
   std::vector<Member> cur;
