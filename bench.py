@@ -43,7 +43,7 @@ DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 3, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"conv_src_sha1": "f48c0cd7a90671a809a89162abd5b5e973127271", "bytes_per_launch": 52.16e9 + 183.99e6}
+NCU_TRAFFIC = {"conv_src_sha1": "f034116c12c17352476ff3c596b3e8d35d9d9165", "bytes_per_launch": 52.161e9 + 183.54e6}
 
 
 # The TPV3 benchmark as Section 3 states it (material, friction, prestress,

@@ -100,9 +100,13 @@ int sbim_step(sbim_handle h, const void* u, const void* v, void* tau);
 /*
  * sbim_step_host -- as sbim_step, with u, v, tau in HOST memory (pageable or
  * pinned).  Copies the inputs to device work buffers, runs the step, copies
- * tau back and waits for the stream.  Section 2.4 step 2 ("copy u and the
- * predicted velocity from FE to SBI") for a caller whose FE solver runs on the
- * host.
+ * tau back and waits for the stream.  Section 2.4 step 2 (displacement and
+ * predicted velocity handed from FE to SBI) for a caller whose FE solver runs on the
+ * host.  The convolution over lags >= 1 (which needs only the stored history)
+ * runs while the inputs are copied and transformed on a side stream; the lag-0
+ * term is added to it afterwards, so tau equals sbim_step's up to the rounding
+ * of that one addition.  With stage profiling on, the steps run in sbim_step's
+ * order instead.
  */
 int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau);
 

@@ -134,7 +134,9 @@ struct sbim_ctx {
   int* d_tile_lmax = nullptr;
   double window = 0.0;
   std::vector<double> h_dT;   // |k| c_s dt per orbit (host copy)
-  void* d_io = nullptr;  // u, v, tau staging for sbim_step_host
+  void* d_io = nullptr;  // u, v, tau staging and zero spectra for sbim_step_host
+  cudaStream_t io_stream = nullptr;          // sbim_step_host: copies in + forward FFT
+  cudaEvent_t io_fork = nullptr, io_join = nullptr;
   cufftHandle plan_fwd = 0, plan_inv = 0;
   bool have_fwd = false, have_inv = false;
 
@@ -305,6 +307,9 @@ void release(sbim_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->io_fork) cudaEventDestroy(c->io_fork);
+  if (c->io_join) cudaEventDestroy(c->io_join);
+  if (c->io_stream) cudaStreamDestroy(c->io_stream);
   delete c;
 }
 
@@ -667,16 +672,59 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
   if (!u || !v || !tau) return fail(SBIM_ERR_ARG, "NULL field pointer");
   sbim_ctx* c = h;
   const size_t bytes = c->field_elems() * c->real_size;
-  if (!c->d_io) CU(cudaMalloc(&c->d_io, 3 * bytes));
+  const size_t hat_bytes = (size_t)3 * c->nbins * 2 * c->real_size;
+  if (!c->d_io) {
+    CU(cudaMalloc(&c->d_io, 3 * bytes + hat_bytes));
+    CU(cudaMemsetAsync((char*)c->d_io + 3 * bytes, 0, hat_bytes, c->stream));
+  }
   char* du = (char*)c->d_io;
   char* dv = du + bytes;
   char* dtau = dv + bytes;
-  CU(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, c->stream));
-  const int rc = sbim_step(h, du, dv, dtau);
-  if (rc != SBIM_OK) return rc;
-  CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
+  void* zero_hat = dtau + bytes;   // all-zero spectra: never written after the memset
+  cudaStream_t st = c->stream;
+  if (c->prof) {   // stage timing wants the plain order
+    CU(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, st));
+    const int rc = sbim_step(h, du, dv, dtau);
+    if (rc != SBIM_OK) return rc;
+  } else {
+    // Every lag >= 1 of Eq. (SBI)'s convolution reads only the stored history,
+    // so it runs while u and v cross to the device and are transformed on the
+    // side stream.  The convolution first sees zero spectra (its ring slot
+    // holds zeros, lag 0 adds nothing); the lag-0 pass then stores the new
+    // spectra and adds w(0) D_n to chunk 0's partial sums, as sbim_step_repeat
+    // does.  Equal to sbim_step up to the order of that one addition.
+    if (!c->io_stream) {
+      CU(cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&c->io_fork, cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&c->io_join, cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(c->io_fork, st));
+    CU(cudaStreamWaitEvent(c->io_stream, c->io_fork, 0));
+    CU(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, c->io_stream));
+    CU(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, c->io_stream));
+    int rc = sbim::handle_fft_forward(c, du, c->io_stream);
+    if (rc != SBIM_OK) return rc;
+    CU(cudaEventRecord(c->io_join, c->io_stream));
+    sbim::StepArgs a = step_args(c);
+    a.uhat = zero_hat;
+    if (c->variant >= 1)
+      CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st));
+    else
+      CU(sbim::launch_conv(a, c->prec, c->kahan, st));
+    CU(cudaStreamWaitEvent(st, c->io_join, 0));
+    a.uhat = c->d_uhat;
+    CU(sbim::launch_repeat_lag0(a, c->prec, st));
+    CU(sbim::launch_assemble(a, c->prec, c->kahan, st));
+    rc = sbim::handle_fft_inverse(c, st);
+    if (rc != SBIM_OK) return rc;
+    rc = sbim::handle_epilogue(c, dv, dtau, st);
+    if (rc != SBIM_OK) return rc;
+    ++c->n;
+    c->can_repeat = true;
+  }
+  CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
   return sbim_check_device(h);
 }
 

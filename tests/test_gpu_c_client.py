@@ -2,7 +2,8 @@
 client is compiled with nvcc against include/sbim.h and the in-tree
 libsbim.so, steps a half-space through a seeded history with device buffers
 (sbim_step) and host buffers (sbim_step_host), and its tractions match the
-FP64 oracle within the FP32 bound; the two entry points agree bit for bit."""
+FP64 oracle within the FP32 bound; the two entry points agree to within the
+rounding of the lag-0 addition, which the host-buffer step makes last."""
 import os
 import shutil
 import subprocess
@@ -54,7 +55,8 @@ def test_c_client_matches_oracle(client, tmp_path, n1, n3, n_cut, side, steps):
     o = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
     worst = 0.0
     for m in range(steps):
-        assert np.array_equal(out[m, 0], out[m, 1])
+        # host buffers: the lag-0 term is added after the other lags
+        assert np.abs(out[m, 0] - out[m, 1]).max() <= 1e-6 * np.abs(out[m, 0]).max()
         ref = o.step(hist.u(m).astype(np.float32).astype(np.float64),
                      hist.v(m).astype(np.float32).astype(np.float64))["tau"]
         for c in range(3):

@@ -120,18 +120,67 @@ def test_far_field_and_uniform_mode():
 
 
 def test_step_host_matches_device_step():
+    """The host-buffer entry point overlaps the input copies with the
+    convolution over lags >= 1 and adds the lag-0 term last: equal to the
+    device step up to that one rounding; with stage profiling on it runs in the
+    device step's order and is bit-identical."""
     from paper_2102_08756_gb300.sbim import SBIM
     n, dx = 32, 100.0
     dt = 0.3 * dx / CP
     hist = separable_history(n, n, n * dx, n * dx, 12, dt, CS, seed=9)
-    a = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
-    b = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
-    for m in range(12):
-        u = hist.u(m).astype(np.float32)
-        v = hist.v(m).astype(np.float32)
-        t_dev = a.step(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
-        t_host = b.step_host(u, v)
-        np.testing.assert_array_equal(t_dev, t_host)
+    for profiled in (False, True):
+        a = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
+        b = SBIM(n, n, n * dx, n * dx, CS, CP, RHO, dt, 8, 1, "fp32", True)
+        if profiled:
+            b.set_profiling(True)
+        for m in range(12):
+            u = hist.u(m).astype(np.float32)
+            v = hist.v(m).astype(np.float32)
+            t_dev = a.step(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
+            t_host = b.step_host(u, v)
+            if profiled:
+                np.testing.assert_array_equal(t_dev, t_host)
+            else:
+                assert np.abs(t_host - t_dev).max() <= 1e-6 * np.abs(t_dev).max()
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1), ("fp32", 0),
+                                             ("bf16x2", 1), ("bf16", 0)])
+@pytest.mark.parametrize("variant,lags_per_cta,window", [(1, 0, 0.0), (0, 0, 0.0), (2, 3, 0.0),
+                                                         (1, 0, 6.0)])
+def test_step_host_overlap_matches_oracle(precision, kahan, variant, lags_per_cta, window):
+    """The overlapped host-buffer step against the oracle on a rectangular grid
+    over several orbit tiles: ring wrap-around (steps > n_cut), several lag
+    chunks, a truncation window, both convolution kernels; a following
+    sbim_step_repeat re-evaluates the level it computed."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    n1, n3, L1, L3, n_cut, steps = 48, 32, 4800.0, 3200.0, 17, 24
+    dt = 0.3 * (L1 / n1) / CP
+    hist = separable_history(n1, n3, L1, L3, steps + 1, dt, CS, seed=77, spectrum="k2")
+    g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, -1, precision, kahan)
+    g.set_conv_config(variant, lags_per_cta)
+    o = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, -1, window=window)
+    if window > 0:
+        g.set_window(window)
+    rdt = np.float64 if precision == "fp64" else np.float32
+    err = 0.0
+    for m in range(steps):
+        u, v = hist.u(m), hist.v(m)
+        t = g.step_host(u.astype(rdt), v.astype(rdt)).astype(np.float64)
+        ref = o.step(u.astype(rdt).astype(np.float64), v.astype(rdt).astype(np.float64))["tau"]
+        err = max(err, rel_l2(t, ref))
+    # re-evaluate the last level with the next displacement
+    u2, v2 = hist.u(steps), hist.v(steps)
+    t2 = g.step_repeat(torch.from_numpy(u2.astype(rdt)).cuda(),
+                       torch.from_numpy(v2.astype(rdt)).cuda()).double().cpu().numpy()
+    o.rewind()
+    ref2 = o.step(u2.astype(rdt).astype(np.float64), v2.astype(rdt).astype(np.float64))["tau"]
+    err = max(err, rel_l2(t2, ref2))
+    g.check()
+    g.close()
+    assert err < TOL[precision], err
 
 
 def test_reset_restarts_history():
