@@ -284,20 +284,46 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           // field -> (kernel, component): 11:xi, 33:perp, 22:2, 12:2, 12:xi (re, im)
           constexpr int kern[kFields] = {0, 0, 2, 2, 1, 1, 3, 3, 3, 3};
           constexpr int comp[kFields] = {0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
+          if constexpr (sizeof(R) == 4) {
+            // (re, im) of one field share weight and value: one two-lane op each
 #pragma unroll
-          for (int f = 0; f < kFields; ++f) {
-            R y = KAHAN ? -cmp[g][f] : acc[g][f];
+            for (int f = 0; f < kFields; f += 2) {
+              float2 y = KAHAN ? make_float2(-cmp[g][f], -cmp[g][f + 1])
+                               : make_float2(acc[g][f], acc[g][f + 1]);
 #pragma unroll
-            for (int k = 0; k < KS; ++k) {
-              const C d = D[k][comp[f]][j];
-              y = fma(w[k][kern[f]], (f & 1) ? d.y : d.x, y);
+              for (int k = 0; k < KS; ++k) {
+                const R wk = w[k][kern[f]];
+                y = fma2(make_float2(wk, wk), D[k][comp[f]][j], y);
+              }
+              if (KAHAN) {
+                const float2 s = make_float2(acc[g][f], acc[g][f + 1]);
+                const float2 t = add2(s, y);
+                const float2 e = sub2(sub2(t, s), y);
+                acc[g][f] = t.x;
+                acc[g][f + 1] = t.y;
+                cmp[g][f] = e.x;
+                cmp[g][f + 1] = e.y;
+              } else {
+                acc[g][f] = y.x;
+                acc[g][f + 1] = y.y;
+              }
             }
-            if (KAHAN) {
-              const R t = acc[g][f] + y;
-              cmp[g][f] = (t - acc[g][f]) - y;
-              acc[g][f] = t;
-            } else {
-              acc[g][f] = y;
+          } else {
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) {
+              R y = KAHAN ? -cmp[g][f] : acc[g][f];
+#pragma unroll
+              for (int k = 0; k < KS; ++k) {
+                const C d = D[k][comp[f]][j];
+                y = fma(w[k][kern[f]], (f & 1) ? d.y : d.x, y);
+              }
+              if (KAHAN) {
+                const R t = acc[g][f] + y;
+                cmp[g][f] = (t - acc[g][f]) - y;
+                acc[g][f] = t;
+              } else {
+                acc[g][f] = y;
+              }
             }
           }
         }

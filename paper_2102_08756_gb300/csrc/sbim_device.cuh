@@ -176,6 +176,35 @@ __device__ __forceinline__ void lag_weights(const T4* __restrict__ tab, unsigned
   w[3] = l0 * a.w + l1 * b.w + l2 * c.w + l3 * d.w;
 }
 
+// Two-lane float arithmetic of the sm_100 family: one instruction applies the
+// same operation to both halves of a (re, im) pair, each rounded as the scalar
+// instruction rounds it.
+__device__ __forceinline__ unsigned long long pack2(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(c)));
+  return unpack2(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(d);
+}
+
 template <int KAHAN, class R>
 __device__ __forceinline__ void kadd(R& s, R& c, R w, R x) {
   if (KAHAN) {
