@@ -564,7 +564,7 @@ int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double c
   // default convolution launch: the shapes the autotuner measured fastest on
   // GB300 at 1024^2 x 4096 (3 stages x 2 lags x 3 CTAs/SM for float and bf16
   // hi-only, 2 x 4 x 2 for bf16 hi/lo, 3 x 1 x 2 for double)
-  c->variant = precision == SBIM_FP64 ? 1 : (precision == SBIM_BF16X2 ? 3 : 2);
+  c->variant = precision == SBIM_FP64 ? 1 : 2;
   const int rc = create_impl(c);
   if (rc != SBIM_OK) {
     const std::string msg = g_err;

@@ -86,6 +86,15 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
       : "memory");
 }
 
+// Whether the next stage's table nodes are loaded during a stage's arithmetic
+// (hides their L2 latency, at KS x 16 floats of registers per thread).  The
+// compensated BF16 kernels, whose unpacked records and Kahan terms already
+// fill the register file, interpolate each stage's weights in place instead.
+template <class S, int KAHAN> struct PrefetchNodes { static constexpr bool value = true; };
+template <bool LO> struct PrefetchNodes<dev::StoreBF16<LO>, 1> {
+  static constexpr bool value = false;
+};
+
 template <class S>
 __host__ __device__ constexpr int seg_bytes() { return kOrbitTile * S::kRecBytes; }
 template <class S, int KS>
@@ -215,9 +224,10 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
     if (tid == 0)
       for (int s = 0; s < min(NS - 1, nst); ++s) issue(s);
 
-    // weights of stage 0
+    constexpr bool PF = PrefetchNodes<S, KAHAN>::value;
+    // weights of stage 0 (prefetching shapes)
     R wn[KS][4];
-    {
+    if constexpr (PF) {
       T4 nd[KS][4];
 #pragma unroll
       for (int k = 0; k < KS; ++k)
@@ -251,16 +261,27 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       const int mb = mf + i * KS;
       const int kk = min(KS, m1 - mb);
       R w[KS][4];
-#pragma unroll
-      for (int k = 0; k < KS; ++k)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[k][q] = wn[k][q];
       // table nodes of the next stage, in flight during this stage's arithmetic
       const int mn = mb + KS;
-      T4 nd[KS][4];
+      T4 nd[PF ? KS : 1][4];
+      if constexpr (PF) {
 #pragma unroll
-      for (int k = 0; k < KS; ++k)
-        if (mn + k < m1) fetch_nodes(tab, (unsigned long long)(mn + k) * us, nd[k]);
+        for (int k = 0; k < KS; ++k)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w[k][q] = wn[k][q];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          if (mn + k < m1) fetch_nodes(tab, (unsigned long long)(mn + k) * us, nd[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (mb + k < m1 && mb + k < lo) {
+            lag_weights(tab, (unsigned long long)(mb + k) * us, dT, w[k]);
+          } else {
+            w[k][0] = w[k][1] = w[k][2] = w[k][3] = (R)0;
+          }
+        }
+      }
 
       const unsigned char* stage = smem + (gi % NS) * STAGE;
 #pragma unroll
@@ -328,12 +349,14 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           }
         }
       }
+      if constexpr (PF) {
 #pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        if (mn + k < m1 && mn + k < lo) {
-          interp_nodes(nd[k], (unsigned long long)(mn + k) * us, dT, wn[k]);
-        } else {
-          wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
+        for (int k = 0; k < KS; ++k) {
+          if (mn + k < m1 && mn + k < lo) {
+            interp_nodes(nd[k], (unsigned long long)(mn + k) * us, dT, wn[k]);
+          } else {
+            wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
+          }
         }
       }
     }
