@@ -43,7 +43,7 @@ DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 2, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"conv_src_sha1": "356698011959291f06c392447aedd552cb7d1016", "bytes_per_launch": 52.160e9 + 183.69e6}
+NCU_TRAFFIC = {"conv_src_sha1": "2441d01ed0673ce4b30497592b19f36e58a35381", "bytes_per_launch": 52.159e9 + 183.25e6}
 
 
 # The TPV3 benchmark as Section 3 states it (material, friction, prestress,

@@ -25,6 +25,8 @@
 // returns without writing its partial sums.
 #pragma once
 
+#include <type_traits>
+
 #include "../../include/sbim.h"
 #include "sbim_device.cuh"
 
@@ -305,8 +307,11 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           // field -> (kernel, component): 11:xi, 33:perp, 22:2, 12:2, 12:xi (re, im)
           constexpr int kern[kFields] = {0, 0, 2, 2, 1, 1, 3, 3, 3, 3};
           constexpr int comp[kFields] = {0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
-          if constexpr (sizeof(R) == 4) {
-            // (re, im) of one field share weight and value: one two-lane op each
+          if constexpr (sizeof(R) == 4 && !std::is_same<S, dev::StoreF32>::value) {
+            // BF16 history: (re, im) of one field share weight and value, one
+            // two-lane op each (the issue-bound kernels gain 10-12 %; the FP32
+            // kernels, HBM-bound, keep scalar FMAs, which their batched launch
+            // measured faster with)
 #pragma unroll
             for (int f = 0; f < kFields; f += 2) {
               float2 y = KAHAN ? make_float2(-cmp[g][f], -cmp[g][f + 1])
