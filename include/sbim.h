@@ -203,6 +203,19 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
                   long long* hist_bytes, long long* table_nodes);
 
 /*
+ * sbim_plan -- the spectral layout sbim_create builds for a grid, computed on
+ * the host without touching the device, so that device memory can be budgeted
+ * before any handle exists.  Outputs as sbim_get_info's (any pointer may be
+ * NULL): n_modes, n_slots (|k|-sorted orbit records x 4 members, padding
+ * included) and hist_bytes (the ring buffer of n_cut steps at `precision`).
+ * Bins are grouped by exact |k| when L1 / L3 is a ratio of integers up to 4096.
+ * SBIM_ERR_ARG for the grid, n_cut and precision rules of sbim_create.
+ * Library utility: the paper has no counterpart.
+ */
+int sbim_plan(int n1, int n3, double L1, double L3, int n_cut, int precision,
+              long long* n_modes, long long* n_slots, long long* hist_bytes);
+
+/*
  * sbim_set_profiling / sbim_stage_times -- per-stage device time.  While
  * profiling is on, every sbim_step records CUDA events on the handle's stream
  * around its stages; sbim_stage_times waits for them and returns the summed

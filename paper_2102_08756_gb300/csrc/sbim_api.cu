@@ -173,6 +173,16 @@ void period_ratio(const sbim_ctx& c, long long& a, long long& b) {
   }
 }
 
+// Bytes of one 4-member history record (all planes) per precision.
+long long history_record_bytes(int prec) {
+  switch (prec) {
+    case SBIM_FP64: return 64;
+    case SBIM_FP32: return 32;
+    case SBIM_BF16X2: return 2 * 16;   // hi and lo planes
+    default: return 16;
+  }
+}
+
 // Group the half-spectrum bins into |k|-sorted orbits of <= 4 members.
 void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_orb) {
   long long ra, rb;
@@ -376,16 +386,8 @@ int create_impl(sbim_ctx* c) {
   if (c->variant >= 1) CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant));
 
   // history size
-  long long rec_bytes = 0;
-  int planes = 1;
-  switch (c->prec) {
-    case SBIM_FP64: rec_bytes = 64; break;
-    case SBIM_FP32: rec_bytes = 32; break;
-    case SBIM_BF16X2: rec_bytes = 16; planes = 2; break;
-    case SBIM_BF16: rec_bytes = 16; break;
-  }
   c->plane_records = (long long)c->n_cut * 3 * c->n_orb_pad;
-  c->hist_bytes = (size_t)c->plane_records * rec_bytes * planes;
+  c->hist_bytes = (size_t)c->plane_records * history_record_bytes(c->prec);
   const size_t part_bytes = (size_t)c->nchunks * 4 * sbim::kFields * c->n_orb_pad * c->real_size;
   const size_t cplx = 2 * c->real_size;
   size_t free_b = 0, total_b = 0;
@@ -542,6 +544,30 @@ int handle_shape(sbim_handle c, int* precision, int* kahan, int* variant, void**
 
 extern "C" {
 
+int sbim_plan(int n1, int n3, double L1, double L3, int n_cut, int precision,
+              long long* n_modes, long long* n_slots, long long* hist_bytes) {
+  g_err.clear();
+  if (n1 < 2 || n3 < 2 || (n1 & 1) || (n3 & 1))
+    return fail(SBIM_ERR_ARG, "n1 and n3 must be even and >= 2 (got %d, %d)", n1, n3);
+  if ((long long)n1 * n3 > (1LL << 28)) return fail(SBIM_ERR_ARG, "grid too large");
+  if (!(L1 > 0) || !(L3 > 0)) return fail(SBIM_ERR_ARG, "L1 and L3 must be positive");
+  if (n_cut < 1) return fail(SBIM_ERR_ARG, "n_cut must be >= 1");
+  if (precision < SBIM_FP64 || precision > SBIM_BF16) return fail(SBIM_ERR_ARG, "bad precision");
+  sbim_ctx c;
+  c.n1 = n1; c.n3 = n3; c.L1 = L1; c.L3 = L3; c.n_cut = n_cut; c.prec = precision;
+  c.nh = n1 / 2 + 1;
+  c.nbins = n3 * c.nh;
+  std::vector<Member> mem;
+  std::vector<double> q_orb;
+  plan_orbits(c, mem, q_orb);
+  const long long pad =
+      ((long long)q_orb.size() + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
+  if (n_modes) *n_modes = c.nbins;
+  if (n_slots) *n_slots = pad * 4;
+  if (hist_bytes) *hist_bytes = (long long)n_cut * 3 * pad * history_record_bytes(precision);
+  return SBIM_OK;
+}
+
 int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double cs, double cp,
                 double rho, double dt, int n_cut, int side, int precision, int kahan,
                 void* stream) {
@@ -562,8 +588,8 @@ int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double c
   c->kahan = precision == SBIM_FP64 ? 0 : (kahan ? 1 : 0);
   c->stream = (cudaStream_t)stream;
   // default convolution launch: the shapes the autotuner measured fastest on
-  // GB300 at 1024^2 x 4096 (3 stages x 2 lags x 3 CTAs/SM for float and bf16
-  // hi-only, 2 x 4 x 2 for bf16 hi/lo, 3 x 1 x 2 for double)
+  // GB300 at 1024^2 x 4096 (shape 2 for every float-class history: 3 stages x
+  // 2 lags x 3 CTAs/SM, 6 x 2 x 3 for bf16 hi-only; 3 x 1 x 2 for double)
   c->variant = precision == SBIM_FP64 ? 1 : 2;
   const int rc = create_impl(c);
   if (rc != SBIM_OK) {

@@ -47,6 +47,7 @@ def lib():
     L.sbim_step_repeat.argtypes = [vp, vp, vp, vp]
     L.sbim_get_step.argtypes = [vp, ctypes.POINTER(ll)]
     L.sbim_get_info.argtypes = [vp] + [ctypes.POINTER(ll)] * 4
+    L.sbim_plan.argtypes = [i, i, d, d, i, i] + [ctypes.POINTER(ll)] * 3
     L.sbim_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     L.sbim_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.sbim_set_profiling.argtypes = [vp, i]
@@ -93,7 +94,7 @@ def lib():
     L.sbim_last_error.restype = ctypes.c_char_p
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
                  "sbim_set_far_field",
-                 "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_set_profiling",
+                 "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_plan", "sbim_set_profiling",
                  "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device", "sbim_set_window",
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
@@ -161,6 +162,15 @@ def sbim_get_info(h):
     vals = [ctypes.c_longlong() for _ in range(4)]
     _check(lib().sbim_get_info(h, *[ctypes.byref(v) for v in vals]))
     return dict(zip(("n_modes", "n_slots", "hist_bytes", "table_nodes"), (v.value for v in vals)))
+
+
+def sbim_plan(n1, n3, L1, L3, n_cut, precision):
+    """Layout sbim_create would build (host only): n_modes, n_slots, hist_bytes."""
+    vals = [ctypes.c_longlong() for _ in range(3)]
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().sbim_plan(int(n1), int(n3), float(L1), float(L3), int(n_cut), prec,
+                           *[ctypes.byref(v) for v in vals]))
+    return dict(zip(("n_modes", "n_slots", "hist_bytes"), (v.value for v in vals)))
 
 
 def sbim_save(h):

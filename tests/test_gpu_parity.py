@@ -13,6 +13,7 @@ import pytest
 from oracle.sbim_oracle import (KernelTable, Material, ModeSet, SBIMOracle,
                                 apply_modal_operator, trapezoid_weights)
 from paper_2102_08756_gb300.synth import config_large, config_small, separable_history
+from tests._layout import expected_slots
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -341,29 +342,6 @@ def test_degenerate_grids(precision, kahan, grid, variant):
     assert es < TOL[precision] and et < TOL[precision], (es, et)
 
 
-def _expected_slots(n1, n3, L1, L3):
-    """Member slots of the orbit layout from first principles: bins grouped by
-    their exact |k|^2 (rational arithmetic), a Nyquist bin counting 2 members
-    (the corner 4), each class packed into records of 4 without splitting a bin,
-    records padded to whole tiles of 128."""
-    from fractions import Fraction
-    classes = {}
-    for r3 in range(n3):
-        j3 = r3 if r3 <= n3 // 2 else r3 - n3
-        for j1 in range(n1 // 2 + 1):
-            key = (Fraction(j1) / Fraction(L1)) ** 2 + (Fraction(j3) / Fraction(L3)) ** 2
-            classes.setdefault(key, []).append((2 if j1 == n1 // 2 else 1) * (2 if r3 == n3 // 2 else 1))
-    records = 0
-    for sizes in classes.values():
-        fill = 0
-        for m in sizes:
-            if fill + m > 4:
-                records, fill = records + 1, 0
-            fill += m
-        records += 1
-    return 4 * (-(-records // 128) * 128)
-
-
 @pytest.mark.parametrize("grid", [(64, 32, 6400.0, 3200.0), (48, 32, 4800.0, 3200.0),
                                   (40, 24, 4000.0, 2520.3)])
 def test_rectangular_orbits_group_equal_wavenumbers(grid):
@@ -371,10 +349,13 @@ def test_rectangular_orbits_group_equal_wavenumbers(grid):
     (equal spacings, L1/L3 = 2 and 3/2; and a period ratio with no small
     fraction, grouped in floating point), so the history carries no more
     padding than the classes force; parity over several orbit tiles."""
-    from paper_2102_08756_gb300.sbim import SBIM
+    from paper_2102_08756_gb300.sbim import SBIM, sbim_plan
     n1, n3, L1, L3 = grid
     g = SBIM(n1, n3, L1, L3, CS, CP, RHO, 0.3 * (L1 / n1) / CP, 8, 1, "fp32", 1)
-    assert g.info()["n_slots"] == _expected_slots(n1, n3, L1, L3)
+    info = g.info()
+    assert info["n_slots"] == expected_slots(n1, n3, L1, L3)
+    plan = sbim_plan(n1, n3, L1, L3, 8, "fp32")
+    assert plan == {k: info[k] for k in plan}
     g.close()
     for precision, kahan in (("fp64", 0), ("fp32", 1)):
         es, et = run_parity(n1, n3, L1, L3, 40, -1, 47, precision, kahan, seed=n1 + n3,
