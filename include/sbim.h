@@ -235,8 +235,8 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
  *                 4 stages x 2 lags x 2 CTAs/SM, 3 x 2 x 3, 2 x 4 x 2 (FP32 / BF16
  *                 hi-lo), 8 x 2 x 2, 6 x 2 x 3, 4 x 4 x 2 (BF16 hi-only),
  *                 3 x 1, 4 x 1, 2 x 2 at 2 CTAs/SM (FP64); 0: per-thread register
- *                 prefetch, per-term compensated sums.  Default: 2 for float and
- *                 bf16 hi-only history, 3 for bf16 hi/lo, 1 for double (the
+ *                 prefetch, per-term compensated sums.  Default: 2 for float,
+ *                 bf16 hi/lo and bf16 hi-only history, 1 for double (the
  *                 fastest shapes measured on GB300 at 1024^2 x 4096).
  *   lags_per_cta  lags one CTA convolves (0 = automatic: ~16 waves of resident CTAs)
  * Both variants compute the same sums to within float rounding.  May reallocate
