@@ -6,8 +6,8 @@ product path (the CUDA library behind ``include/sbim.h`` and its Python
 binding) never imports, links or executes anything under ``oracle/``, and this
 module imports nothing from the product package.
 
-What is computed (Albertini, Elbanna & Kammer, "A three-dimensional hybrid
-finite element -- spectral boundary integral method", Section 2.3, Eq. (SBI)):
+What is computed (Albertini, Elbanna & Kammer, arXiv:2102.08756, Section 2.3,
+Eq. (SBI)):
 
     tau_i(x1, x3, t) = tau_i^inf - eta_ij (mu / c_s) du_j/dt + s_i(x1, x3, t)
 
