@@ -88,6 +88,38 @@ def test_rupture_matches_oracle(precision, tol):
     g.close()
 
 
+def test_fault_solution_independent_of_strip_width():
+    """The paper's validation of the hybrid scheme by varying the strip width
+    L2 (Sections 3 and 4): the slip rate at a station off the nucleation patch
+    is the same for L2 = 4 dx and 8 dx, and each GPU run (FP64) follows the
+    oracle's run of the same slab."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n1 = n3 = 32
+    h, steps = 100.0, 45
+    dt = 0.3 * h / CP
+    mu_s, tau0 = _rupture_setup(n1, n3)
+    station = (n3 // 2, n1 // 2 + 4)
+    traces = {}
+    for n2 in (4, 8):
+        o = HybridOracle(SlabMesh(n1, n2, n3, h, fault=True), CS, CP, RHO, dt, n_cut=steps + 1,
+                         fault=FaultLaw(mu_s, 0.525, 0.02, tau0, 120e6))
+        g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, "fp64", True, True)
+        g.set_fault(mu_s, tau0, 0.525, 0.02, 120e6)
+        got, ref = [], []
+        for _ in range(steps):
+            o.step()
+            g.step()
+            got.append(float(g.fault_fields()[1][0][station]))
+            ref.append(o.slip_rate[0][station])
+        g.close()
+        got, ref = np.array(got), np.array(ref)
+        assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
+        traces[n2] = got
+    a, b = traces[4], traces[8]
+    assert np.abs(a).max() > 1.0                     # the rupture reached the station
+    assert np.abs(a - b).max() < 0.1 * np.abs(a).max()
+
+
 def test_gpu_sbim_boundaries_reproduce_an_unbounded_slab():
     """The coupled GPU path: a force pulse in a thin slab with SBIM half-spaces
     moves like the same pulse in a thick free slab until reflections return."""
