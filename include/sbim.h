@@ -301,6 +301,9 @@ int sbim_selftest_wait_timeout(sbim_handle h);
  * that every GPU which loads the library keeps until the process exits; it holds
  * the kernel table and the lag-chunk partial sums.  Limits (SBIM_ERR_ARG
  * otherwise): n3 (n1/2+1) <= 655,296 bins, and |k|max c_s dt (n_lags - 1) <= 8191.9.
+ * uhat_hist and fhat must be 8-byte aligned memory of the current device (or
+ * managed memory); host pointers and misaligned pointers return SBIM_ERR_ARG
+ * before any launch.
  * The first call on a device (and any call with a new cp/cs or a longer history
  * range) resolves the array's device address and builds the kernel table, waiting
  * for the stream; make that first call before any stream capture.  All calls

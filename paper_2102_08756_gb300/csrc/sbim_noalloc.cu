@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -212,6 +213,27 @@ void gl16(double* x, double* w) {
   }
 }
 
+// The kernels read and write the spectra as float2: a pointer that is not
+// 8-byte aligned, or one the device cannot reach, would fault the caller's
+// context.  Accept device memory of the current device and managed memory.
+int check_spectrum_pointer(const void* p, const char* what, int dev) {
+  if ((uintptr_t)p % alignof(float2) != 0)
+    return na_fail(SBIM_ERR_ARG, "%s is not %zu-byte aligned", what, alignof(float2));
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(SBIM_ERR_ARG, "%s: cudaPointerGetAttributes: %s", what, cudaGetErrorString(e));
+  }
+  if (at.type == cudaMemoryTypeManaged) return SBIM_OK;
+  if (at.type != cudaMemoryTypeDevice)
+    return na_fail(SBIM_ERR_ARG, "%s is not device memory", what);
+  if (at.device != dev)
+    return na_fail(SBIM_ERR_ARG, "%s belongs to device %d, the current device is %d", what,
+                   at.device, dev);
+  return SBIM_OK;
+}
+
 }  // namespace
 
 extern "C" int sbim_spectral_response_noalloc(int n1, int n3, double L1, double L3, double cs,
@@ -247,6 +269,9 @@ extern "C" int sbim_spectral_response_noalloc(int n1, int n3, double L1, double 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(SBIM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev >= kMaxDevices) return na_fail(SBIM_ERR_ARG, "device index %d not supported", dev);
+  int rc = check_spectrum_pointer(uhat_hist, "uhat_hist", dev);
+  if (rc == SBIM_OK) rc = check_spectrum_pointer(fhat, "fhat", dev);
+  if (rc != SBIM_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
 
   std::lock_guard<std::mutex> lock(g_mu);

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle.sbim_oracle import adjoint_sequence
+from tests._errors import assert_finite
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,7 +46,7 @@ def test_adjoint_matches_oracle_transpose(precision, tol, n1, n3, n_cut, steps, 
         h.step_adjoint(tbd[m], ub[m], vb[m])
     h.check()
     h.close()
-    ub, vb = ub.double().cpu().numpy(), vb.double().cpu().numpy()
+    ub, vb = assert_finite(ub, "u_bar"), assert_finite(vb, "v_bar")
     for m in range(steps):
         for c in range(3):
             e = np.linalg.norm(ub[m, c] - ub_ref[m, c]) / np.linalg.norm(ub_ref[m, c])

@@ -7,6 +7,7 @@ import pytest
 
 from oracle.sbim_oracle import SBIMOracle
 from paper_2102_08756_gb300.synth import separable_history
+from tests._errors import assert_finite
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,6 +73,7 @@ def test_batch_equals_members_stepped_alone(shape, lags):
             ref = [alone[k].step(u[k], v[k]) for k in range(len(MEMBERS))]
             stream.synchronize()
             for k in range(len(MEMBERS)):
+                assert_finite(tau[k], "batched tau")
                 assert torch.equal(tau[k], ref[k]), (m, k)
             for k, o in enumerate(oracles):
                 r = o.step(u[k].double().cpu().numpy(), v[k].double().cpu().numpy())["tau"]

@@ -13,6 +13,7 @@ import pytest
 
 from oracle.sbim_oracle import SBIMOracle
 from paper_2102_08756_gb300.synth import separable_history
+from tests._errors import Worst, assert_finite
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,7 +54,8 @@ def test_c_client_matches_oracle(client, tmp_path, n1, n3, n_cut, side, steps):
     assert r.returncode == 0, r.stderr
     out = np.fromfile(dst, dtype=np.float32).reshape(steps, 2, 3, n3, n1)
     o = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
-    worst = 0.0
+    assert_finite(out, "client output")
+    worst = Worst()
     for m in range(steps):
         # host buffers: the lag-0 term is added after the other lags
         assert np.abs(out[m, 0] - out[m, 1]).max() <= 1e-6 * np.abs(out[m, 0]).max()
@@ -62,5 +64,5 @@ def test_c_client_matches_oracle(client, tmp_path, n1, n3, n_cut, side, steps):
         for c in range(3):
             nr = np.linalg.norm(ref[c])
             if nr > 0:
-                worst = max(worst, np.linalg.norm(out[m, 0, c] - ref[c]) / nr)
-    assert worst < 1e-5, worst
+                worst.update(np.linalg.norm(out[m, 0, c] - ref[c]) / nr)
+    assert worst.value < 1e-5, worst

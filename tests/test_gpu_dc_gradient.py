@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle.fem_oracle import FaultLaw, HybridOracle, SlabMesh, dc_gradient, forward_record
+from tests._errors import assert_finite
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,6 +47,8 @@ def test_dc_gradient_matches_oracle(precision, tol):
     assert out.dtype == dtype
     J = (out.double() * torch.from_numpy(tb).to(out.device)).sum()
     (g,) = torch.autograd.grad(J, dc)
+    assert_finite(out, "boundary tractions")
+    assert_finite(g, "dJ/dDc")
     np.testing.assert_allclose(out.detach().double().cpu().numpy(), taus, rtol=0,
                                atol=(1e-7 if precision == "fp64" else 5e-3) * np.abs(taus).max())
     assert abs(float(g) - ref.sum()) < tol * abs(ref.sum()), (float(g), ref.sum())

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle.fem_oracle import FaultLaw, HybridOracle, SlabMesh
+from tests._errors import Worst, assert_finite, rel_l2_field
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -19,8 +20,7 @@ def built():
     __graft_entry__.build()
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+rel = rel_l2_field
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
@@ -75,16 +75,18 @@ def test_rupture_matches_oracle(precision, tol):
                      fault=FaultLaw(mu_s, 0.525, 0.02, tau0, 120e6))
     g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, precision, True, True)
     g.set_fault(mu_s, tau0, 0.525, 0.02, 120e6)
-    worst, peak = 0.0, 0.0
+    worst, peak = Worst(), 0.0
     for _ in range(steps):
         o.step()
         g.step()
         slip, rate, trac = (x.double().cpu().numpy() for x in g.fault_fields())
+        assert_finite(slip, "slip")
+        assert_finite(trac, "traction")
         peak = max(peak, np.abs(o.slip_rate).max())
         if np.linalg.norm(o.slip_rate) > 0:
-            worst = max(worst, rel(rate, o.slip_rate))
+            worst.update(rel(rate, o.slip_rate))
     assert peak > 1.0
-    assert worst < tol, worst
+    assert worst.value < tol, worst
     g.close()
 
 
@@ -109,7 +111,7 @@ def test_fault_solution_independent_of_strip_width():
         for _ in range(steps):
             o.step()
             g.step()
-            got.append(float(g.fault_fields()[1][0][station]))
+            got.append(float(assert_finite(g.fault_fields()[1])[0][station]))
             ref.append(o.slip_rate[0][station])
         g.close()
         got, ref = np.array(got), np.array(ref)
@@ -141,14 +143,14 @@ def test_gpu_sbim_boundaries_reproduce_an_unbounded_slab():
 
     thin = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, "fp32", True, False)
     thick = Hybrid(n1, n2 + 2 * pad, n3, h, CS, CP, RHO, dt, steps + 1, "fp32", False, False)
-    worst = 0.0
+    worst = Worst()
     for n in range(1, steps + 1):
         thin.step(source(n2 + 1, 0, n))
         thick.step(source(n2 + 2 * pad + 1, pad, n))
         ut = thin.get_state()[0].double().cpu().numpy()
         ur = thick.get_state()[0].double().cpu().numpy()[pad:pad + n2 + 1]
-        worst = max(worst, rel(ut, ur))
-    assert worst < 0.08, worst
+        worst.update(rel(ut, ur))
+    assert worst.value < 0.08, worst
 
 
 def test_coupled_configuration_fp32_against_fp64_and_mirror_symmetry():

@@ -13,6 +13,7 @@ import pytest
 from oracle.sbim_oracle import (KernelTable, Material, ModeSet, SBIMOracle,
                                 apply_modal_operator, trapezoid_weights)
 from paper_2102_08756_gb300.synth import config_large, config_small, separable_history
+from tests._errors import Worst, assert_finite, rel_l2
 from tests._layout import expected_slots
 
 torch = pytest.importorskip("torch")
@@ -28,11 +29,6 @@ def built():
         pytest.skip("no CUDA device")
     import __graft_entry__
     __graft_entry__.build()
-
-
-def rel_l2(got, ref):
-    return max(np.linalg.norm(got[c] - ref[c]) / max(np.linalg.norm(ref[c]), 1e-300)
-               for c in range(3))
 
 
 def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
@@ -51,7 +47,7 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
     g_s.set_conv_config(variant)
     if tau_inf is not None:
         g_tau.set_far_field(tau_inf)
-    err_s = err_t = 0.0
+    err_s, err_t = Worst(), Worst()
     zero = torch.zeros((3, n3, n1), dtype=tdt, device="cuda")
     for m in range(steps):
         u = hist.u(m).astype(ndt)
@@ -61,15 +57,17 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
         s = g_s.step(ud, zero).double().cpu().numpy()
         rt = o_tau.step(u.astype(np.float64), v.astype(np.float64))
         rs = o_s.step(u.astype(np.float64), np.zeros((3, n3, n1)))
+        assert_finite(s, "s")
+        assert_finite(t, "tau")
         if np.linalg.norm(rs["s"]) > 0:
-            err_s = max(err_s, rel_l2(s, rs["s"]))
-            err_t = max(err_t, rel_l2(t, rt["tau"]))
+            err_s.update(rel_l2(s, rs["s"]))
+            err_t.update(rel_l2(t, rt["tau"]))
     assert g_tau.n == steps
     g_tau.check()
     g_s.check()
     g_tau.close()
     g_s.close()
-    return err_s, err_t
+    return err_s.value, err_t.value
 
 
 @pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1), ("fp32", 0),
@@ -139,6 +137,8 @@ def test_step_host_matches_device_step():
             v = hist.v(m).astype(np.float32)
             t_dev = a.step(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
             t_host = b.step_host(u, v)
+            assert_finite(t_dev, "device-buffer tau")
+            assert_finite(t_host, "host-buffer tau")
             if profiled:
                 np.testing.assert_array_equal(t_dev, t_host)
             else:
@@ -166,22 +166,22 @@ def test_step_host_overlap_matches_oracle(precision, kahan, variant, lags_per_ct
     if window > 0:
         g.set_window(window)
     rdt = np.float64 if precision == "fp64" else np.float32
-    err = 0.0
+    err = Worst()
     for m in range(steps):
         u, v = hist.u(m), hist.v(m)
         t = g.step_host(u.astype(rdt), v.astype(rdt)).astype(np.float64)
         ref = o.step(u.astype(rdt).astype(np.float64), v.astype(rdt).astype(np.float64))["tau"]
-        err = max(err, rel_l2(t, ref))
+        err.update(rel_l2(t, ref))
     # re-evaluate the last level with the next displacement
     u2, v2 = hist.u(steps), hist.v(steps)
     t2 = g.step_repeat(torch.from_numpy(u2.astype(rdt)).cuda(),
                        torch.from_numpy(v2.astype(rdt)).cuda()).double().cpu().numpy()
     o.rewind()
     ref2 = o.step(u2.astype(rdt).astype(np.float64), v2.astype(rdt).astype(np.float64))["tau"]
-    err = max(err, rel_l2(t2, ref2))
+    err.update(rel_l2(t2, ref2))
     g.check()
     g.close()
-    assert err < TOL[precision], err
+    assert err.value < TOL[precision], err
 
 
 def test_reset_restarts_history():
@@ -198,6 +198,7 @@ def test_reset_restarts_history():
                             torch.from_numpy(hist.v(m).astype(np.float32)).cuda()).cpu().numpy()
                      for m in range(7)])
     for x, y in zip(*outs):
+        assert_finite(x)
         np.testing.assert_array_equal(x, y)
 
 
@@ -217,6 +218,7 @@ def test_explicit_lag_chunking(lags_per_cta):
         v = torch.from_numpy(hist.v(m).astype(np.float32)).cuda()
         a = ref.step(u, v).double().cpu().numpy()
         b = alt.step(u, v).double().cpu().numpy()
+        assert_finite(a)
         if np.linalg.norm(a) > 0:
             assert rel_l2(b, a) < 2e-6
     alt.check()
@@ -284,10 +286,11 @@ def test_large_boundary_sampled_modes(precision, kahan, tol, variant):
     hist_rev = np.einsum("rl,rcq->lcq", gl, Uh)
     F_ref = apply_modal_operator(modes, mat, side, w, hist_rev, hist_rev[0])
     got = F_gpu[:, r3, j1]
+    assert_finite(F_gpu, "s spectrum")
     errs = [np.linalg.norm(got[k] - F_ref[k]) / np.linalg.norm(F_ref[k]) for k in range(3)]
     print(f"\nPRECISION-REPORT 1024x1024 n_cut=4096 {precision} kahan={kahan} variant={variant}: "
           f"relative L2 error of s_1, s_2, s_3 spectra = {errs[0]:.3e} {errs[1]:.3e} {errs[2]:.3e}")
-    assert max(errs) < tol, errs
+    assert np.max(errs) < tol, errs
 
 
 def _window_avoiding_integers(dT, window):
@@ -319,15 +322,15 @@ def test_truncation_window_matches_oracle(variant, grid, window):
     g.set_window(window)
     hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=31, spectrum="k2")
     zero = torch.zeros((3, n3, n1), device="cuda")
-    worst = 0.0
+    worst = Worst()
     for m in range(steps):
         u = hist.u(m).astype(np.float32)
-        s = g.step(torch.from_numpy(u).cuda(), zero).double().cpu().numpy()
+        s = assert_finite(g.step(torch.from_numpy(u).cuda(), zero), "s")
         r = o.step(u.astype(np.float64), np.zeros((3, n3, n1)))["s"]
         if np.linalg.norm(r) > 0:
-            worst = max(worst, rel_l2(s, r))
+            worst.update(rel_l2(s, r))
     g.check()
-    assert worst < 1e-5, worst
+    assert worst.value < 1e-5, worst
 
 
 @pytest.mark.parametrize("precision,kahan", [("fp64", 0), ("fp32", 1)])

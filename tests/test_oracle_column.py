@@ -13,6 +13,7 @@ agreement bounds any error in the kernels, their signs and the coupling."""
 import numpy as np
 
 from oracle.sbim_oracle import SBIMOracle
+from tests._errors import Worst, max_abs_rel
 
 CS, CP, RHO = 3464.0, 6000.0, 2670.0
 MU = RHO * CS * CS
@@ -63,7 +64,7 @@ def _oracle_errors(ts, tr, dt, t_end):
     o = SBIMOracle(N1, N3, N1 * DX, N3 * DX, CS, CP, RHO, dt, steps + 1, +1)
     ph = np.exp(1j * K * np.arange(N1) * DX)
     scale = np.abs(tr).max()
-    worst = 0.0
+    worst = Worst()
     for n in range(steps):
         t = n * dt
         u = np.zeros((3, N3, N1))
@@ -75,8 +76,8 @@ def _oracle_errors(ts, tr, dt, t_end):
         amp = np.array([(tau[c, 0] * np.conj(ph)).sum() * 2 / N1 for c in (0, 1)])
         ref = np.array([np.interp(t, ts, tr[:, c].real) + 1j * np.interp(t, ts, tr[:, c].imag)
                         for c in (0, 1)])
-        worst = max(worst, np.abs(amp - ref).max() / scale)
-    return worst
+        worst.update(max_abs_rel(amp, ref, scale))
+    return worst.value
 
 
 def test_in_plane_mode_matches_finite_difference_column():
