@@ -12,8 +12,13 @@ Metric: mode-history MACs per second, 5 complex-by-real MACs per (Fourier
 mode, lag) pair over the n3 (n1/2 + 1) half-spectrum modes and min(n+1, n_cut)
 lags.  The history (51.6 GB) is far larger than L2, so no flush is needed.
 
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
-Under torchrun (N > 1) every rank runs an independent replica of the workload.
+``--workload adjoint-sbim`` times the adjoint update instead (sbim_step_adjoint:
+the transpose of the same update, taken in reverse time, on the same grid and
+history; the same convolution kernel and the same MAC count per step).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead,
+on every host core.  Under torchrun (N > 1) every rank runs an independent
+replica of the workload.
 """
 from __future__ import annotations
 
@@ -26,8 +31,9 @@ import subprocess
 import sys
 import time
 
-# The FP64 oracle baseline is timed on one host thread (its "cores" field): pin
-# the BLAS / OpenMP pools before numpy starts them.
+# The FP64 oracle baseline runs one worker process per host core, each on one
+# BLAS thread: pin the BLAS / OpenMP pools before numpy starts them (spawned
+# workers inherit the setting).
 for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, "1")
 
@@ -89,7 +95,8 @@ def parse():
                    help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
-    p.add_argument("--workload", default="sbim", choices=["sbim", "coupled", "ensemble", "adjoint", "tpv3"],
+    p.add_argument("--workload", default="sbim",
+                   choices=["sbim", "adjoint-sbim", "coupled", "ensemble", "adjoint", "tpv3"],
                    help="sbim: the single half-space update (default); coupled: FEM slab + fault "
                         "between two half-spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -109,8 +116,10 @@ def workload(args):
     return c
 
 
-def workload_name(c, precision, kahan):
-    return (f"single half-space SBIM step, {c['n1']}x{c['n3']} boundary, dx=100 m, "
+def workload_name(c, precision, kahan, adjoint=False):
+    head = ("adjoint SBIM step (transpose of the update, reverse time)" if adjoint
+            else "single half-space SBIM step")
+    return (f"{head}, {c['n1']}x{c['n3']} boundary, dx=100 m, "
             f"{c['n_cut']}-lag history, {precision} history"
             + (" + Kahan accumulation" if kahan and precision != "fp64" else ""))
 
@@ -234,31 +243,43 @@ def dist_setup(args):
 _TABLES = {}
 
 
-def oracle_sample(c, sample_modes, seed, side=1):
+def oracle_table(c):
+    """The oracle's kernel table for the workload (built once per process)."""
+    from oracle.sbim_oracle import KernelTable
+    eta = c["cp"] / c["cs"]
+    L = c["n_cut"]
+    dT_max = np.sqrt(2.0) * np.pi / min(c["L1"] / c["n1"], c["L3"] / c["n3"]) * c["cs"] * c["dt"]
+    key = (eta, L, round(dT_max, 12))
+    if key not in _TABLES:
+        _TABLES[key] = KernelTable(eta, dT_max * L + 1)
+    return _TABLES[key]
+
+
+def oracle_sample(c, sample_modes, seed, side=1, pick=None, table=None):
     """A bounded sample of the workload for the FP64 oracle: ``sample_modes``
-    random Fourier modes with their full-history weights and a random
-    history of n_cut steps (the kernel table is built once per process)."""
-    from oracle.sbim_oracle import KernelTable, Material, ModeSet, trapezoid_weights
+    random Fourier modes (or the flat half-spectrum indices ``pick``) with their
+    full-history weights and a random history of n_cut steps."""
+    from oracle.sbim_oracle import Material, ModeSet, trapezoid_weights
     rng = np.random.default_rng(seed)
     nh = c["n1"] // 2 + 1
-    pick = rng.choice(c["n3"] * nh, size=sample_modes, replace=False)
+    if pick is None:
+        pick = rng.choice(c["n3"] * nh, size=sample_modes, replace=False)
+    pick = np.asarray(pick)
+    sample_modes = len(pick)
     modes = ModeSet.build(c["n1"], c["n3"], c["L1"], c["L3"], r3=pick // nh, j1=pick % nh)
     mat = Material(c["cs"], c["cp"], c["rho"])
     L = c["n_cut"]
-    dT_max = np.sqrt(2.0) * np.pi / min(c["L1"] / c["n1"], c["L3"] / c["n3"]) * c["cs"] * c["dt"]
-    key = (mat.eta, L, round(dT_max, 12))
-    if key not in _TABLES:
-        _TABLES[key] = KernelTable(mat.eta, dT_max * L + 1)
-    kt = _TABLES[key]
+    kt = table if table is not None else oracle_table(c)
     dT = modes.q * c["cs"] * c["dt"]
     w = np.stack([trapezoid_weights(d, L, kt) for d in dT], axis=1)
     hist = rng.normal(size=(L, 3, sample_modes)) + 1j * rng.normal(size=(L, 3, sample_modes))
     return dict(modes=modes, mat=mat, side=side, w=w, hist=hist, L=L, n=sample_modes)
 
 
-def time_oracle(sample, min_seconds=0.0):
+def time_oracle(sample, min_seconds=0.0, min_reps=1):
     """Run the oracle's per-mode operator (convolution + assembly, FP64, one
-    thread) on the sample until ``min_seconds`` elapsed; returns (MAC/s, s, reps)."""
+    thread) on the sample until ``min_seconds`` elapsed and ``min_reps`` passes
+    are done; returns (MAC/s, s, reps)."""
     from oracle.sbim_oracle import apply_modal_operator
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -266,9 +287,96 @@ def time_oracle(sample, min_seconds=0.0):
                              sample["hist"], sample["hist"][0])
         reps += 1
         el = time.perf_counter() - t0
-        if el >= min_seconds:
+        if el >= min_seconds and reps >= min_reps:
             break
     return sample["n"] * sample["L"] * MACS_PER_PAIR * reps / el, el, reps
+
+
+def _oracle_worker(conn, barrier, c, pick, seed, table):
+    """One oracle worker process: builds its sample of disjoint modes, then
+    times the per-mode operator on command, starting with the other workers."""
+    smp = oracle_sample(c, len(pick), seed, pick=pick, table=table)
+    conn.send("ready")
+    while True:
+        cmd = conn.recv()
+        if cmd is None:
+            break
+        min_seconds, min_reps = cmd
+        barrier.wait()
+        rate, el, reps = time_oracle(smp, min_seconds=min_seconds, min_reps=min_reps)
+        conn.send((rate * el, el))
+    conn.close()
+
+
+class OraclePool:
+    """The FP64 oracle on ``workers`` host cores: one spawned process per core
+    (one BLAS thread each), each on its own disjoint random sample of
+    ``modes_per_worker`` modes with full-history weights.  ``run`` starts every
+    worker together and returns the aggregate MAC/s (all MACs over the slowest
+    worker's time) and that time.  Spawned, not forked, so a process holding a
+    CUDA context can start it."""
+
+    def __init__(self, c, workers, modes_per_worker, seed):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        table = oracle_table(c)
+        perm = np.random.default_rng(seed).permutation(n_modes(c))
+        self.workers = workers
+        self.barrier = ctx.Barrier(workers)
+        self.conns, self.procs = [], []
+        for i in range(workers):
+            a, b = ctx.Pipe()
+            pick = perm[i * modes_per_worker:(i + 1) * modes_per_worker]
+            p = ctx.Process(target=_oracle_worker, args=(b, self.barrier, c, pick, seed + 1 + i, table),
+                            daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for a in self.conns:
+            if a.recv() != "ready":
+                raise RuntimeError("oracle worker failed to start")
+
+    def run(self, min_seconds=0.0, min_reps=1):
+        for a in self.conns:
+            a.send((min_seconds, min_reps))
+        res = [a.recv() for a in self.conns]
+        slowest = max(el for _, el in res)
+        return sum(m for m, _ in res) / slowest, slowest
+
+    def close(self):
+        for a in self.conns:
+            try:
+                a.send(None)
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+
+
+def cpu_workers():
+    return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline_leg(c, modes_per_worker=1024, seconds=10.0):
+    """The FP64 oracle timed on the host: every core at once (the reported
+    value), and one thread alone beside it."""
+    one = oracle_sample(c, sample_modes=modes_per_worker, seed=7)
+    rate1, secs1, reps1 = time_oracle(one, min_seconds=seconds / 2)
+    del one
+    workers = cpu_workers()
+    pool = OraclePool(c, workers, modes_per_worker, seed=7)
+    try:
+        rate, secs = pool.run(min_seconds=seconds)
+    finally:
+        pool.close()
+    return {"value": rate, "unit": "MAC/s", "cores": workers, "kind": "oracle",
+            "sample": (f"{workers} worker processes (one per host core, one BLAS thread each), "
+                       f"each {modes_per_worker} disjoint random modes x {c['n_cut']} lags of the "
+                       f"full-history per-mode operator, repeated for {secs:.1f} s; one thread "
+                       f"alone: {rate1:.3e} MAC/s ({reps1} passes, {secs1:.1f} s)"),
+            "single_thread": rate1, "host": host_cpu()}
 
 
 def host_cpu():
@@ -291,13 +399,19 @@ def run_reference(args):
     if rank != 0:
         return
     c = workload(args)
-    sample = oracle_sample(c, sample_modes=256, seed=100)
-    for _ in range(args.warmup):
-        time_oracle(sample)
-    rates = [time_oracle(sample)[0] for _ in range(args.steps)]
+    workers = cpu_workers()
+    per = 256
+    pool = OraclePool(c, workers, per, seed=100)
+    try:
+        for _ in range(args.warmup):
+            pool.run()
+        rates = [pool.run()[0] for _ in range(args.steps)]
+    finally:
+        pool.close()
     value = float(np.mean(rates))
-    desc = (f"{sample['n']} random modes x {sample['L']} lags per step: the oracle's full-history "
-            f"per-mode operator, {args.steps} steps")
+    desc = (f"{workers} worker processes (one per host core, one BLAS thread each), each "
+            f"{per} disjoint random modes x {c['n_cut']} lags per step: the oracle's "
+            f"full-history per-mode operator, {args.steps} steps")
     line = {
         "impl": "reference", "metric": "SBIM mode-history MACs/s", "value": value, "unit": "MAC/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -306,7 +420,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": workload_name(c, "fp64", 0) + " (FP64 CPU oracle, sampled modes)",
                    "n1": c["n1"], "n3": c["n3"], "n_cut": c["n_cut"]},
-        "cpu_baseline": {"value": value, "unit": "MAC/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MAC/s", "cores": workers, "kind": "oracle",
                          "sample": desc, "host": host_cpu()},
         "e2e": {"value": value, "unit": "MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,6 +444,7 @@ def run_native(args):
     c = workload(args)
     n1, n3, n_cut, dt = c["n1"], c["n3"], c["n_cut"], c["dt"]
     prec = args.precision
+    adjoint = args.workload == "adjoint-sbim"
     tdt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.current_stream()
     g = SBIM(n1, n3, c["L1"], c["L3"], c["cs"], c["cp"], c["rho"], dt, n_cut, 1, prec,
@@ -348,6 +463,15 @@ def run_native(args):
     u = torch.empty((3, n3, n1), device=dev, dtype=tdt)
     v = torch.empty_like(u)
     tau = torch.empty_like(u)
+    if adjoint:
+        # the adjoint takes a traction cotangent tau_bar (here the seeded
+        # boundary field) and writes u_bar and v_bar
+        def step(x, y, out):
+            g.step_adjoint(x, out, y_bar)
+        y_bar = torch.empty_like(u)
+    else:
+        def step(x, y, out):
+            g.step(x, y, out)
 
     def fields(m, out_u, out_v):
         torch.mul(U[0], float(gts[0, m]), out=out_u)
@@ -362,7 +486,7 @@ def run_native(args):
     # fill the history (untimed)
     for m in range(n_cut):
         fields(m, u, v)
-        g.step(u, v, tau)
+        step(u, v, tau)
     # inputs of the warm-up and timed steps, resident in HBM before timing
     us = [torch.empty_like(u) for _ in range(W + K)]
     vs = [torch.empty_like(u) for _ in range(W + K)]
@@ -374,7 +498,7 @@ def run_native(args):
         best, table = autotune(g, us[0], vs[0])
         tuned = {"best": best, "trials": table}
     for k in range(W):
-        g.step(us[k], vs[k], tau)
+        step(us[k], vs[k], tau)
     torch.cuda.synchronize()
 
     g.set_profiling(True)
@@ -388,7 +512,7 @@ def run_native(args):
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for k in range(W, W + K):
-            g.step(us[k], vs[k], tau)
+            step(us[k], vs[k], tau)
         e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -420,7 +544,9 @@ def run_native(args):
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and adjoint:
+        e2e = e2e_adjoint(g, us[-1], K, world, dev, macs_step)
+    elif not args.no_e2e:
         hu = torch.empty((3, n3, n1), dtype=tdt, pin_memory=True)
         hv = torch.empty_like(hu).pin_memory()
         ht = torch.empty_like(hu).pin_memory()
@@ -450,18 +576,13 @@ def run_native(args):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        smp = oracle_sample(c, sample_modes=1024, seed=7)
-        rate, secs, reps = time_oracle(smp, min_seconds=10.0)
-        cpu = {"value": rate, "unit": "MAC/s", "cores": 1, "kind": "oracle",
-               "sample": (f"{smp['n']} random modes x {smp['L']} lags of the full-history "
-                          f"per-mode operator, repeated {reps}x ({secs:.1f} s, one thread)"),
-               "host": host_cpu()}
+        cpu = cpu_baseline_leg(c)
     line = {
         "metric": "SBIM mode-history MACs/s", "value": value, "unit": "MAC/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": workload_name(c, prec, args.kahan), "n1": n1, "n3": n3,
+        "config": {"workload": workload_name(c, prec, args.kahan, adjoint), "n1": n1, "n3": n3,
                    "n_cut": n_cut, "precision": prec, "kahan": int(bool(args.kahan)),
                    "conv_variant": args.variant if args.variant >= 0 else DEFAULT_VARIANT[prec],
                    "window": args.window, "mode_lag_pairs": pairs,
@@ -485,6 +606,40 @@ def run_native(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def e2e_adjoint(g, tb_dev, K, world, dev, macs_step):
+    """End to end through sbim_step_adjoint with host buffers: every step copies
+    the cotangent tau_bar from pinned host memory to the device, runs the
+    adjoint update, and copies u_bar and v_bar back, on the handle's stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ht = torch.empty(tb_dev.shape, dtype=tb_dev.dtype, pin_memory=True)
+    hu = torch.empty_like(ht).pin_memory()
+    hv = torch.empty_like(ht).pin_memory()
+    ht.copy_(tb_dev.cpu())
+    dt_, du, dv = (torch.empty_like(tb_dev) for _ in range(3))
+
+    def one():
+        dt_.copy_(ht, non_blocking=True)
+        g.step_adjoint(dt_, du, dv)
+        hu.copy_(du, non_blocking=True)
+        hv.copy_(dv, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        one()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / K, dev)
+    fb = ht.numel() * ht.element_size()
+    return {"value": job_throughput(macs_step, e2e_s, world), "unit": "MAC/s",
+            "h2d_bytes_per_step": fb, "d2h_bytes_per_step": 2 * fb, "ms_per_step": e2e_s * 1e3,
+            "api": "sbim_step_adjoint with pinned host copies on the handle's stream"}
 
 
 def run_coupled(args):

@@ -45,7 +45,7 @@ typedef enum {
     SBIM_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
     SBIM_ERR_FFT = -4,       /* a cuFFT call failed */
     SBIM_ERR_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
-    SBIM_ERR_NONFINITE = -6, /* reserved: non-finite input detected */
+    SBIM_ERR_NONFINITE = -6, /* non-finite input detected (opt-in, sbim_set_check_finite) */
     SBIM_ERR_STATE = -7      /* call not valid in the handle's current state */
 } sbim_status;
 
@@ -214,6 +214,24 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
  */
 int sbim_plan(int n1, int n3, double L1, double L3, int n_cut, int precision,
               long long* n_modes, long long* n_slots, long long* hist_bytes);
+
+/*
+ * sbim_set_check_finite -- opt-in check of every step's input for NaN and
+ * infinity.  Eq. (SBI) (Section 2.3) convolves each mode's whole displacement
+ * history, so one non-finite value in u would spoil every traction of the next
+ * n_cut steps; with the check on, sbim_step, sbim_step_host and sbim_step_repeat
+ * (u and v) and sbim_step_adjoint (tau_bar) first run one reduction kernel over
+ * their input fields on the handle's stream and read its flag on the host.  If a
+ * value is not finite the call returns SBIM_ERR_NONFINITE before anything else is
+ * enqueued: no output is written, the history and the step counter are unchanged,
+ * and the next call with finite input continues exactly as if the refused call
+ * had not been made.  The read synchronises the handle's stream once per step
+ * (the check is off by default: steps are then stream-ordered with no host
+ * sync).  sbim_step_host takes its plain (non-overlapped) order while the check
+ * is on.  Batched steps (sbim_batch_*) do not check.  Library utility: the paper
+ * has no counterpart.
+ */
+int sbim_set_check_finite(sbim_handle h, int enable);
 
 /*
  * sbim_set_profiling / sbim_stage_times -- per-stage device time.  While

@@ -130,6 +130,8 @@ struct sbim_ctx {
   void* d_s = nullptr;
   long long* d_step = nullptr;
   int* d_err = nullptr;
+  int* d_nonfinite = nullptr;  // flag of the opt-in input check
+  bool check_finite = false;
   int* d_lmax = nullptr;
   int* d_tile_lmax = nullptr;
   double window = 0.0;
@@ -313,7 +315,7 @@ void release(sbim_ctx* c) {
   void* ptrs[] = {c->d_bin, c->d_dir, c->d_wout, c->d_dT, c->d_ustep, c->d_muq,
                   c->d_tab64, c->d_tab32, c->d_gl, c->d_hist, c->d_part, c->d_uhat,
                   c->d_fhat, c->d_s, c->d_step, c->d_err, c->d_io, c->d_lmax,
-                  c->d_tile_lmax};
+                  c->d_tile_lmax, c->d_nonfinite};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -612,9 +614,28 @@ namespace {
 // matrix is Hermitian in the (xi, 2, perp) frame ([a, ib; -ib, d] and a real
 // perp entry), so the transpose of R2C -> A -> C2R/N is the same map; applied to
 // the tau_bar sequence in reverse time it gives the time-reversed correlation.
+// The opt-in input check: a reduction over the step's inputs, read back on the
+// host before anything of the step is enqueued, so a refused step leaves the
+// handle exactly as it was.
+int check_inputs(sbim_ctx* c, const void* a, const void* b) {
+  CU(sbim::launch_nonfinite_check(c->prec, a, b, (long long)c->field_elems(), c->d_nonfinite,
+                                  c->stream));
+  int flag = 0;
+  CU(cudaMemcpyAsync(&flag, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (flag)
+    return fail(SBIM_ERR_NONFINITE, "non-finite value (NaN or infinity) in the step's input; "
+                                    "the step was not taken");
+  return SBIM_OK;
+}
+
 int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoint,
              bool repeat = false) {
   cudaStream_t st = c->stream;
+  if (c->check_finite) {
+    const int rc = check_inputs(c, in, adjoint ? nullptr : aux);
+    if (rc != SBIM_OK) return rc;
+  }
   if (repeat) {                     // back to the level being re-evaluated
     CU(sbim::launch_rewind(c->d_step, st));
     --c->n;
@@ -708,7 +729,7 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
   char* dtau = dv + bytes;
   void* zero_hat = dtau + bytes;   // all-zero spectra: never written after the memset
   cudaStream_t st = c->stream;
-  if (c->prof) {   // stage timing wants the plain order
+  if (c->prof || c->check_finite) {   // stage timing and the input check want the plain order
     CU(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, st));
     const int rc = sbim_step(h, du, dv, dtau);
@@ -778,6 +799,13 @@ int sbim_set_window(sbim_handle h, double window) {
                      h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->window = window;
+  return SBIM_OK;
+}
+
+int sbim_set_check_finite(sbim_handle h, int enable) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (enable && !h->d_nonfinite) CU(cudaMalloc(&h->d_nonfinite, sizeof(int)));
+  h->check_finite = enable != 0;
   return SBIM_OK;
 }
 

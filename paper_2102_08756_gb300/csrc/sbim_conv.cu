@@ -242,6 +242,22 @@ __global__ void adjoint_epilogue_kernel(const R* __restrict__ tau_bar, R* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
 }
 
+// Opt-in input check (sbim_set_check_finite): sets *flag if any of the n values
+// of a or b (b may be NULL) is NaN or infinite.  One block-wide vote per pass and
+// at most one store per block.
+template <class R>
+__global__ void __launch_bounds__(256) nonfinite_kernel(const R* __restrict__ a,
+                                                        const R* __restrict__ b, long long n,
+                                                        int* __restrict__ flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    bad |= !isfinite(a[i]);
+    if (b) bad |= !isfinite(b[i]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1;
+}
+
 // Re-evaluation of the current level with a new displacement (sbim_step_repeat).
 // Every lag >= 1 of the truncated convolution is unchanged, so chunk 0's partial
 // sums take w(0) (D_new - D_old) and the ring slot takes D_new; the assembly then
@@ -385,6 +401,23 @@ cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st
     case SBIM_BF16: repeat_lag0_kernel<StoreBF16<false>><<<grid, kOrbitTile, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_check(int precision, const void* a, const void* b, long long n,
+                                   int* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  long long blocks = (n + threads - 1) / threads;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  if (precision == SBIM_FP64)
+    nonfinite_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double*)a,
+                                                                   (const double*)b, n, flag);
+  else
+    nonfinite_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float*)a,
+                                                                  (const float*)b, n, flag);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,9 @@ cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
 cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_rewind(long long* step, cudaStream_t st);
+// *flag = 1 if any of the n values of a or b (b may be NULL) is not finite, else 0.
+cudaError_t launch_nonfinite_check(int precision, const void* a, const void* b, long long n,
+                                   int* flag, cudaStream_t st);
 cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st);
 cudaError_t launch_epilogue(int precision, const void* s_field, const void* v, void* tau,
                             long long plane, const double coef[3], const double tau_inf[3],

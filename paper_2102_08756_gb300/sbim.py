@@ -51,6 +51,7 @@ def lib():
     L.sbim_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     L.sbim_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.sbim_set_profiling.argtypes = [vp, i]
+    L.sbim_set_check_finite.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
     L.sbim_set_conv_config.argtypes = [vp, i, i]
     L.sbim_set_window.argtypes = [vp, d]
@@ -95,6 +96,7 @@ def lib():
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
                  "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_plan", "sbim_set_profiling",
+                 "sbim_set_check_finite",
                  "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device", "sbim_set_window",
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
@@ -193,6 +195,10 @@ def sbim_load(h, buf):
 
 def sbim_set_profiling(h, enable):
     _check(lib().sbim_set_profiling(h, int(enable)))
+
+
+def sbim_set_check_finite(h, enable):
+    _check(lib().sbim_set_check_finite(h, int(enable)))
 
 
 def sbim_stage_times(h):
@@ -490,6 +496,9 @@ class SBIM:
 
     def set_profiling(self, enable=True):
         sbim_set_profiling(self.h, enable)
+
+    def set_check_finite(self, enable=True):
+        sbim_set_check_finite(self.h, enable)
 
     def stage_times(self):
         return sbim_stage_times(self.h)

@@ -9,11 +9,12 @@ terms
 
 with U_r a real random field on the periodic boundary grid (three displacement
 components) and g_r a band-limited temporal signal that starts from rest.
-Two spatial spectra are offered: ``"band"`` (flat amplitude for
-|k| <= k_cut, zero above) and ``"k2"`` (amplitude 1 / (1 + (|k|/k0)^2), the
-k^-2 falloff of a rupture-like field).  ``sparse`` keeps only a seeded random
-subset of Fourier bins, whose exact spectra are returned so that large grids
-can be checked bin by bin.
+Three spatial spectra are offered: ``"band"`` (flat amplitude for
+|k| <= k_cut, zero above), ``"k2"`` (amplitude 1 / (1 + (|k|/k0)^2), the
+k^-2 falloff of a rupture-like field) and ``"flat"`` (the same amplitude at
+every wavenumber).  ``sparse`` keeps only a seeded random subset of Fourier
+bins, ``bins`` an explicit one; their exact spectra are returned so that large
+grids can be checked bin by bin.
 
 This module is shared input plumbing: it holds none of the boundary-integral
 arithmetic and is used identically by the tests, the benchmark and the
@@ -62,13 +63,18 @@ def _temporal(rng, steps, dt, omega_max, n_sin=8, ramp_steps=20):
 
 
 def separable_history(n1, n3, L1, L3, steps, dt, cs, seed, *, n_terms=4,
-                      spectrum="band", amp_rms=1e-3, sparse=None):
+                      spectrum="band", amp_rms=1e-3, sparse=None, bins=None):
     """Draw a seeded ``SeparableHistory``.
 
     spectrum : "band" -> flat up to a quarter of the Nyquist wavenumber;
-               "k2"   -> amplitude 1/(1+(k/k0)^2), k0 = 2 pi / (32 dx).
+               "k2"   -> amplitude 1/(1+(k/k0)^2), k0 = 2 pi / (32 dx);
+               "flat" -> unit amplitude everywhere.
     sparse   : if an int, only that many random half-spectrum bins per term
                are non-zero (their spectra are exact in ``Uhat``).
+    bins     : if given, flat indices r3 (n1/2+1) + j1 of the half-spectrum
+               bins that are non-zero in every term (plus the partners that
+               the real-field symmetry of the j1 = 0 and j1 = n1/2 columns
+               adds), exact in ``Uhat``.
     """
     rng = np.random.default_rng(seed)
     nh = n1 // 2 + 1
@@ -85,6 +91,8 @@ def separable_history(n1, n3, L1, L3, steps, dt, cs, seed, *, n_terms=4,
     elif spectrum == "k2":
         k0 = 2 * np.pi / (32 * dx)
         shape = 1.0 / (1.0 + (kk / k0) ** 2)
+    elif spectrum == "flat":
+        shape = np.ones_like(kk)
     else:
         raise ValueError(spectrum)
     U = np.empty((n_terms, 3, n3, n1))
@@ -96,9 +104,13 @@ def separable_history(n1, n3, L1, L3, steps, dt, cs, seed, *, n_terms=4,
                 keep = np.zeros(n3 * nh, dtype=bool)
                 keep[rng.choice(n3 * nh, size=min(sparse, n3 * nh), replace=False)] = True
                 spec = spec * keep.reshape(n3, nh)
+            if bins is not None:
+                keep = np.zeros(n3 * nh, dtype=bool)
+                keep[np.asarray(bins)] = True
+                spec = spec * keep.reshape(n3, nh)
             field = np.fft.irfft2(spec, s=(n3, n1))
             sp = np.fft.rfft2(field)                # the spectrum the field really has
-            if sparse is not None:                  # drop FFT round-off outside the bins
+            if sparse is not None or bins is not None:   # drop FFT round-off outside the bins
                 sp[np.abs(sp) < 1e-9 * np.abs(sp).max()] = 0.0
                 field = np.fft.irfft2(sp, s=(n3, n1))
             Uh[r, c] = sp

@@ -10,11 +10,11 @@ bf16 hi-only history (the storage rounding of 2^-17 and 2^-9 per value).
 import numpy as np
 import pytest
 
-from oracle.sbim_oracle import (KernelTable, Material, ModeSet, SBIMOracle,
-                                apply_modal_operator, trapezoid_weights)
+from oracle.sbim_oracle import Material, ModeSet, SBIMOracle
 from paper_2102_08756_gb300.synth import config_large, config_small, separable_history
 from tests._errors import Worst, assert_finite, rel_l2
-from tests._layout import expected_slots
+from tests._layout import expected_slots, square_grid_records
+from tests._sampled import adjoint_spectra, forward_spectra
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -237,60 +237,187 @@ def test_profiling_stage_times():
     assert times["convolution"] > 0
 
 
+def _large_bins(n, rng, n_random=3800):
+    """Half-spectrum bins of an n x n grid for the full-size check: both Nyquist
+    lines (j1 = n/2 and r3 = n/2, with their ends), the bins around k = 0, every
+    bin of the last orbit tile (the highest |k|, corner included) and random
+    bins; returns flat indices r3 (n/2+1) + j1 and the last tile's bins."""
+    nh = n // 2 + 1
+    sel = set()
+    ends = [0, 1, 2, n // 2 - 1, n // 2, n // 2 + 1, n - 2, n - 1]
+    for r3 in ends + list(rng.choice(n, 160, replace=False)):
+        sel.add(int(r3) * nh + n // 2)
+    for j1 in [0, 1, 2, n // 2 - 2, n // 2 - 1, n // 2] + list(rng.choice(nh, 160, replace=False)):
+        sel.add((n // 2) * nh + int(j1))
+    for r3, j1 in [(0, 0), (0, 1), (1, 0), (n - 1, 0), (1, 1), (n - 1, 1), (0, 2), (2, 0),
+                   (2, 1), (n - 2, 1), (1, 2), (n - 1, 2)]:
+        sel.add(r3 * nh + j1)
+    records, padded = square_grid_records(n)
+    last = [b for rec in records[padded - 128:] for b in rec]
+    sel.update(last)
+    sel.update(int(b) for b in rng.choice(n * nh, n_random, replace=False))
+    return np.array(sorted(sel)), set(last), padded
+
+
+def _bin_groups(r3, j1, n1, n3, last_tile):
+    """The groups of checked bins whose relative errors are bounded separately."""
+    flat = r3 * (n1 // 2 + 1) + j1
+    groups = {"all": np.ones(len(r3), bool),
+              "nyquist j1=n1/2": j1 == n1 // 2,
+              "nyquist j3=n3/2": r3 == n3 // 2,
+              "around k=0": (j1 <= 2) & ((r3 <= 2) | (r3 >= n3 - 2)),
+              "last orbit tile": np.isin(flat, list(last_tile))}
+    assert all(m.sum() >= 6 for m in groups.values()), {k: int(m.sum()) for k, m in groups.items()}
+    return groups
+
+
+def _group_errors(got, ref, groups):
+    """Relative L2 per component (3,) on every group of bins."""
+    return {name: np.array([np.linalg.norm(got[k][m] - ref[k][m]) / max(np.linalg.norm(ref[k][m]), 1e-300)
+                            for k in range(3)]) for name, m in groups.items()}
+
+
+_LARGE = {}
+
+
+def _large_case():
+    """Input history, bins and the oracle's s spectra of the full-size check,
+    computed once per module (they do not depend on the history precision)."""
+    if not _LARGE:
+        c = config_large()
+        n1, n3, L1, L3, n_cut, dt = c["n1"], c["n3"], c["L1"], c["L3"], c["n_cut"], c["dt"]
+        checked = [n_cut - 1, n_cut, n_cut + 1, n_cut + 23]
+        bins, last_tile, padded = _large_bins(n1, np.random.default_rng(3003))
+        hist = separable_history(n1, n3, L1, L3, checked[-1] + 1, dt, CS, seed=3003, n_terms=2,
+                                 spectrum="flat", bins=bins)
+        nz = np.nonzero(np.abs(hist.Uhat).sum(axis=(0, 1)) > 0)
+        modes = ModeSet.build(n1, n3, L1, L3, r3=nz[0], j1=nz[1])
+        ref_s = forward_spectra(modes, Material(CS, CP, RHO), -1, dt, n_cut,
+                                hist.Uhat[:, :, nz[0], nz[1]], hist.g, checked)
+        _LARGE.update(checked=checked, hist=hist, last_tile=last_tile, padded=padded,
+                      r3=nz[0], j1=nz[1], modes=modes, ref_s=ref_s)
+    return _LARGE
+
+
 @pytest.mark.parametrize("precision,kahan,tol,variant", [("fp32", 1, 1e-5, -1), ("fp32", 1, 1e-5, 0),
                                                          ("fp32", 0, 1e-5, -1), ("bf16x2", 1, 1e-4, -1),
                                                          ("bf16", 0, 1e-2, -1), ("fp64", 0, 1e-9, -1)])
 def test_large_boundary_sampled_modes(precision, kahan, tol, variant):
-    """1024 x 1024 boundary with the full 4096-lag history (plus wrap-around),
-    in the launch configuration the benchmark times.  Input: two separable
-    terms on 2 x 600 random Fourier bins with exactly known spectra; the last
-    step's non-local traction spectrum (FP64 FFT of the GPU output) is compared
-    bin by bin on those bins with the oracle's per-mode operator."""
+    """1024 x 1024 boundary with the full 4096-lag history, in the launch
+    configuration the benchmark times.  Input: two separable terms with a flat
+    spectrum on about 4,800 half-spectrum bins with exactly known spectra --
+    both Nyquist lines, the bins around k = 0, every bin of the last orbit tile
+    (corner included) and random bins.  At four steps (the last before the ring
+    wraps, the first two after it, and a later one) the traction tau with a
+    non-zero velocity and, by re-evaluating the same level with v = 0
+    (sbim_step_repeat), the non-local term s are compared bin by bin with the
+    oracle's per-mode operator (FP64 FFT of the GPU output); the relative L2
+    error per component is bounded on every group of bins separately."""
     from paper_2102_08756_gb300.sbim import SBIM
     c = config_large()
     n1, n3, L1, L3, n_cut, dt = c["n1"], c["n3"], c["L1"], c["L3"], c["n_cut"], c["dt"]
-    steps = n_cut + 37
+    nh = n1 // 2 + 1
     side = -1
-    hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=3003, n_terms=2,
-                             spectrum="k2", sparse=600)
+    case = _large_case()
+    checked, hist, last_tile, padded = case["checked"], case["hist"], case["last_tile"], case["padded"]
+    steps = checked[-1] + 1
     g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
+    assert g.info()["n_slots"] == 4 * padded
     if variant >= 0:
         g.set_conv_config(variant)
     fdt = torch.float64 if precision == "fp64" else torch.float32
     U = torch.from_numpy(hist.U).to("cuda", fdt)
-    gT = torch.from_numpy(hist.g)
+    gT = hist.g
     zero = torch.zeros((3, n3, n1), device="cuda", dtype=fdt)
     u = torch.empty((3, n3, n1), device="cuda", dtype=fdt)
+    v = torch.empty_like(u)
     tau = torch.empty_like(u)
+    s_out = torch.empty_like(u)
+    got_tau, got_s = {}, {}
     for m in range(steps):
         torch.mul(U[0], float(gT[0, m]), out=u)
         u.add_(U[1], alpha=float(gT[1, m]))
-        g.step(u, zero, tau)
+        if m not in checked:
+            g.step(u, zero, tau)
+            continue
+        gp = gT[:, m - 1]
+        torch.mul(U[0], float((gT[0, m] - gp[0]) / dt), out=v)
+        v.add_(U[1], alpha=float((gT[1, m] - gp[1]) / dt))
+        g.step(u, v, tau)
+        g.step_repeat(u, zero, s_out)
+        got_tau[m] = np.fft.rfft2(assert_finite(tau, "tau"))
+        got_s[m] = np.fft.rfft2(assert_finite(s_out, "s"))
     g.check()
-    F_gpu = np.fft.rfft2(tau.double().cpu().numpy())
     g.close()
 
-    nz = np.nonzero(np.abs(hist.Uhat).sum(axis=(0, 1)) > 0)
-    r3, j1 = nz[0], nz[1]
-    modes = ModeSet.build(n1, n3, L1, L3, r3=r3, j1=j1)
-    mat = Material(CS, CP, RHO)
-    dT = modes.q * CS * dt
-    kt = KernelTable(mat.eta, float(dT.max()) * n_cut + 1)
-    uniq, inv = np.unique(dT, return_inverse=True)
-    wu = np.stack([trapezoid_weights(d, n_cut, kt) for d in uniq], axis=1)
-    w = wu[:, inv, :]
-    nlast = steps - 1
-    lags = np.arange(n_cut)
-    gl = hist.g[:, nlast - lags]                                   # (R, L)
-    Uh = hist.Uhat[:, :, r3, j1]                                   # (R, 3, nsel)
-    hist_rev = np.einsum("rl,rcq->lcq", gl, Uh)
-    F_ref = apply_modal_operator(modes, mat, side, w, hist_rev, hist_rev[0])
-    got = F_gpu[:, r3, j1]
-    assert_finite(F_gpu, "s spectrum")
-    errs = [np.linalg.norm(got[k] - F_ref[k]) / np.linalg.norm(F_ref[k]) for k in range(3)]
-    print(f"\nPRECISION-REPORT 1024x1024 n_cut=4096 {precision} kahan={kahan} variant={variant}: "
-          f"relative L2 error of s_1, s_2, s_3 spectra = {errs[0]:.3e} {errs[1]:.3e} {errs[2]:.3e}")
-    assert np.max(errs) < tol, errs
+    r3, j1, ref_s = case["r3"], case["j1"], case["ref_s"]
+    assert len(r3) >= 4096
+    groups = _bin_groups(r3, j1, n1, n3, last_tile)
+    imp = np.array([1.0, CP / CS, 1.0])
+    worst = {}
+    for n in checked:
+        Vh = np.einsum("r,rcq->cq", (gT[:, n] - gT[:, n - 1]) / dt, hist.Uhat[:, :, r3, j1])
+        ref_t = ref_s[n] - side * (RHO * CS) * imp[:, None] * Vh
+        for what, got, ref in (("s", got_s[n][:, r3, j1], ref_s[n]), ("tau", got_tau[n][:, r3, j1], ref_t)):
+            for name, e in _group_errors(got, ref, groups).items():
+                worst[(what, name)] = np.fmax(worst.get((what, name), np.zeros(3)), e) \
+                    if np.isfinite(e).all() else np.full(3, np.nan)
+    print(f"\nPRECISION-REPORT 1024x1024 n_cut=4096 {precision} kahan={kahan} variant={variant} "
+          f"({len(r3)} bins, steps {checked}): relative L2 error per component, max over steps")
+    for (what, name), e in worst.items():
+        print(f"  {what:3s} {name:18s} {e[0]:.3e} {e[1]:.3e} {e[2]:.3e}")
+    bad = {k: v for k, v in worst.items() if not (np.max(v) < tol)}
+    assert not bad, bad
+
+
+def test_large_boundary_adjoint_sampled_modes():
+    """The adjoint update (sbim_step_adjoint, the transpose of Eq. (SBI) taken in
+    reverse time) at 1024 x 1024 with the full 4096-lag history, FP32 + Kahan, in
+    the launch configuration of the forward benchmark.  The traction cotangent
+    tau_bar is the full-size check's separable history on the same bins; the
+    spectrum of u_bar after four calls (the last before the ring wraps, the
+    first two after, a later one) is compared bin by bin with the oracle's
+    conjugate-transposed modal matrices, and v_bar with the radiation term's
+    transpose -side (mu/c_s) eta tau_bar."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    c = config_large()
+    n1, n3, L1, L3, n_cut, dt = c["n1"], c["n3"], c["L1"], c["L3"], c["n_cut"], c["dt"]
+    side = 1
+    case = _large_case()
+    checked, hist, last_tile = case["checked"], case["hist"], case["last_tile"]
+    r3, j1, modes = case["r3"], case["j1"], case["modes"]
+    g = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, "fp32", True)
+    U = torch.from_numpy(hist.U).to("cuda", torch.float32)
+    tb = torch.empty((3, n3, n1), device="cuda")
+    ub, vb = torch.empty_like(tb), torch.empty_like(tb)
+    got_u, got_v = {}, {}
+    scale = 1e6                               # traction-sized cotangent
+    for m in range(checked[-1] + 1):
+        torch.mul(U[0], float(scale * hist.g[0, m]), out=tb)
+        tb.add_(U[1], alpha=float(scale * hist.g[1, m]))
+        g.step_adjoint(tb, ub, vb)
+        if m in checked:
+            got_u[m] = np.fft.rfft2(assert_finite(ub, "u_bar"))
+            v = assert_finite(vb, "v_bar")
+            t = tb.double().cpu().numpy()
+            imp = np.array([1.0, CP / CS, 1.0])[:, None, None]
+            got_v[m] = np.abs(v + side * RHO * CS * imp * t).max() / np.abs(v).max()
+    g.check()
+    g.close()
+    ref = adjoint_spectra(modes, Material(CS, CP, RHO), side, dt, n_cut, n1, n3,
+                          scale * hist.Uhat[:, :, r3, j1], hist.g, checked)
+    groups = _bin_groups(r3, j1, n1, n3, last_tile)
+    worst = {}
+    for n in checked:
+        for name, e in _group_errors(got_u[n][:, r3, j1], ref[n], groups).items():
+            worst[name] = np.fmax(worst.get(name, np.zeros(3)), e)
+    print(f"\nADJOINT-REPORT 1024x1024 n_cut=4096 fp32 kahan=1 ({len(r3)} bins, calls {checked}): "
+          f"relative L2 error of the u_bar spectra per component, max over calls")
+    for name, e in worst.items():
+        print(f"  {name:18s} {e[0]:.3e} {e[1]:.3e} {e[2]:.3e}")
+    print(f"  v_bar max relative deviation {max(got_v.values()):.3e}")
+    assert all(np.max(e) < 1e-5 for e in worst.values()), worst
+    assert max(got_v.values()) < 1e-6
 
 
 def _window_avoiding_integers(dT, window):
