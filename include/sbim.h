@@ -77,7 +77,11 @@ typedef enum {
  *              legacy default stream
  * The kernel tables are built on the device in double precision.  Returns
  * SBIM_ERR_OOM if the history ring buffer (n_cut x 3 x modes, complex) does not
- * fit in free device memory.  *out is written on success only.
+ * fit in free device memory.  An SBIM_FP64 handle also keeps its convolution
+ * weights, computed once (n_cut x n_slots x 8 bytes; 17.3 GB at 1024^2 x 4096),
+ * when they fit with 512 MB to spare; otherwise it interpolates them from the
+ * table every step, with the same result to rounding.  *out is written on
+ * success only.
  */
 int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3,
                 double cs, double cp, double rho, double dt, int n_cut,

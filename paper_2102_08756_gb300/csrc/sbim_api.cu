@@ -131,6 +131,8 @@ struct sbim_ctx {
   long long* d_step = nullptr;
   int* d_err = nullptr;
   int* d_nonfinite = nullptr;  // flag of the opt-in input check
+  void* d_wts = nullptr;       // FP64 path: precomputed weights [n_cut][n_orb_pad][4] doubles
+  size_t wts_bytes = 0;
   bool check_finite = false;
   int* d_lmax = nullptr;
   int* d_tile_lmax = nullptr;
@@ -315,7 +317,7 @@ void release(sbim_ctx* c) {
   void* ptrs[] = {c->d_bin, c->d_dir, c->d_wout, c->d_dT, c->d_ustep, c->d_muq,
                   c->d_tab64, c->d_tab32, c->d_gl, c->d_hist, c->d_part, c->d_uhat,
                   c->d_fhat, c->d_s, c->d_step, c->d_err, c->d_io, c->d_lmax,
-                  c->d_tile_lmax, c->d_nonfinite};
+                  c->d_tile_lmax, c->d_nonfinite, c->d_wts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -338,6 +340,8 @@ int harvest(sbim_ctx* c, long long upto) {
   }
   return SBIM_OK;
 }
+
+sbim::StepArgs step_args(const sbim_ctx* c);
 
 int create_impl(sbim_ctx* c) {
   c->mu = c->rho * c->cs * c->cs;
@@ -399,6 +403,12 @@ int create_impl(sbim_ctx* c) {
   if (need + (256ull << 20) > free_b)
     return fail(SBIM_ERR_OOM, "need %.2f GB of device memory, %.2f GB free",
                 need / 1e9, free_b / 1e9);
+  // The FP64 path keeps its convolution weights (32 B per orbit and lag) when
+  // they fit beside everything else; without them it interpolates every step.
+  if (dbl) {
+    const size_t wb = (size_t)c->n_cut * c->n_orb_pad * 32;
+    if (need + wb + (512ull << 20) <= free_b) c->wts_bytes = wb;
+  }
 
   CU(cudaMalloc(&c->d_bin, h_bin.size() * sizeof(int)));
   CU(cudaMalloc(&c->d_dir, h_dir.size() * (dbl ? sizeof(double2) : sizeof(float2))));
@@ -417,6 +427,7 @@ int create_impl(sbim_ctx* c) {
   CU(cudaMalloc(&c->d_s, c->field_elems() * c->real_size));
   CU(cudaMalloc(&c->d_step, sizeof(long long)));
   CU(cudaMalloc(&c->d_err, sizeof(int)));
+  if (c->wts_bytes) CU(cudaMalloc(&c->d_wts, c->wts_bytes));
 
   cudaStream_t st = c->stream;
   CU(cudaMemcpyAsync(c->d_bin, h_bin.data(), h_bin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -443,6 +454,7 @@ int create_impl(sbim_ctx* c) {
   CU(cudaMemcpyAsync(c->d_gl, gl, sizeof gl, cudaMemcpyHostToDevice, st));
   CU(sbim::launch_table_build(c->d_tab64, c->d_tab32, c->tab_n, c->tab_h, c->eta, c->d_gl,
                               c->d_gl + 16, st));
+  if (c->d_wts) CU(sbim::launch_weights64(step_args(c), c->d_wts, st));
   CU(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   CU(cudaStreamSynchronize(st));
@@ -471,6 +483,7 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
   a.table = c->prec == SBIM_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
   a.lmax = c->window > 0 ? c->d_lmax : nullptr;
   a.tile_lmax = c->window > 0 ? c->d_tile_lmax : nullptr;
+  a.wts = c->d_wts;
   a.hist = c->d_hist;
   a.step = c->d_step;
   a.err = c->d_err;

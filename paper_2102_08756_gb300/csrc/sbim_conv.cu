@@ -242,6 +242,23 @@ __global__ void adjoint_epilogue_kernel(const R* __restrict__ tau_bar, R* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
 }
 
+// FP64 weights precomputed once per handle: they depend only on (orbit, lag),
+// so the FP64 convolution, bound by the FP64 pipe, streams them beside the
+// history instead of re-interpolating them every step.
+__global__ void __launch_bounds__(256) weights64_kernel(const StepArgs a, Double4* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)a.n_cut * a.n_orb_pad;
+  if (i >= total) return;
+  const int o = (int)(i % a.n_orb_pad);
+  const long long m = i / a.n_orb_pad;
+  double w[4];
+  lag_weights(reinterpret_cast<const Double4*>(a.table), (unsigned long long)m * a.ustep[o],
+              reinterpret_cast<const double*>(a.dT)[o], w);
+  Double4 r;
+  r.x = w[0]; r.y = w[1]; r.z = w[2]; r.w = w[3];
+  out[i] = r;
+}
+
 // Opt-in input check (sbim_set_check_finite): sets *flag if any of the n values
 // of a or b (b may be NULL) is NaN or infinite.  One block-wide vote per pass and
 // at most one store per block.
@@ -401,6 +418,13 @@ cudaError_t launch_repeat_lag0(const StepArgs& a, int precision, cudaStream_t st
     case SBIM_BF16: repeat_lag0_kernel<StoreBF16<false>><<<grid, kOrbitTile, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weights64(const StepArgs& a, void* out, cudaStream_t st) {
+  const long long total = (long long)a.n_cut * a.n_orb_pad;
+  const long long blocks = (total + 255) / 256;
+  weights64_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, reinterpret_cast<Double4*>(out));
   return cudaGetLastError();
 }
 

@@ -99,8 +99,16 @@ template <bool LO> struct PrefetchNodes<dev::StoreBF16<LO>, 1> {
 
 template <class S>
 __host__ __device__ constexpr int seg_bytes() { return kOrbitTile * S::kRecBytes; }
+// FP64 history: a stage also holds each lag's precomputed weights (4 doubles per
+// orbit) when the handle keeps them (StepArgs::wts); the float paths interpolate.
+template <class S>
+__host__ __device__ constexpr int wseg_bytes() {
+  return std::is_same<S, dev::StoreF64>::value ? kOrbitTile * 32 : 0;
+}
 template <class S, int KS>
-__host__ __device__ constexpr int stage_bytes() { return KS * 3 * S::kPlanes * seg_bytes<S>(); }
+__host__ __device__ constexpr int stage_bytes() {
+  return KS * (3 * S::kPlanes * seg_bytes<S>() + wseg_bytes<S>());
+}
 template <class S, int NS, int KS>
 __host__ __device__ constexpr int smem_bytes() { return NS * stage_bytes<S, KS>(); }
 
@@ -145,6 +153,8 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
   using C = typename S::cplx;
   using T4 = typename S::tab4;
   constexpr int SEG = seg_bytes<S>();
+  constexpr int WSEG = wseg_bytes<S>();
+  constexpr int HIST = KS * 3 * S::kPlanes * SEG;   // history part of a stage
   constexpr int STAGE = stage_bytes<S, KS>();
   constexpr int MPC = S::kChunkMembers, NCH = S::kChunks;
 
@@ -203,12 +213,14 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
   if (nst > 0) {
     const unsigned char* hist = reinterpret_cast<const unsigned char*>(a.hist);
     const long long plane_bytes = a.slot_stride * S::kRecBytes;
+    const unsigned char* wts = reinterpret_cast<const unsigned char*>(a.wts);
+    const bool pre = WSEG > 0 && wts != nullptr;   // uniform over the CTA
     auto issue = [&](int s) {
       const int b = (int)((gstage + s) % NS);
       const int mb = mf + s * KS;
       const int kk = min(KS, m1 - mb);
       const unsigned bar = smem_addr(&full[b]);
-      mbar_expect_tx(bar, (unsigned)(kk * 3 * S::kPlanes * SEG));
+      mbar_expect_tx(bar, (unsigned)(kk * (3 * S::kPlanes * SEG + (pre ? WSEG : 0))));
       for (int k = 0; k < kk; ++k) {
         int slot = sn - (mb + k);
         if (slot < 0) slot += a.n_cut;
@@ -221,6 +233,9 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
             const unsigned dst = smem_addr(smem + b * STAGE + ((k * 3 + c) * S::kPlanes + pl) * SEG);
             bulk_g2s(dst, src, SEG, bar);
           }
+        if (pre)
+          bulk_g2s(smem_addr(smem + b * STAGE + HIST + k * WSEG),
+                   wts + ((long long)(mb + k) * orb + tile0) * 32, WSEG, bar);
       }
     };
     if (tid == 0)
@@ -229,7 +244,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
     constexpr bool PF = PrefetchNodes<S, KAHAN>::value;
     // weights of stage 0 (prefetching shapes)
     R wn[KS][4];
-    if constexpr (PF) {
+    if constexpr (PF) if (!pre) {
       T4 nd[KS][4];
 #pragma unroll
       for (int k = 0; k < KS; ++k)
@@ -266,7 +281,25 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       // table nodes of the next stage, in flight during this stage's arithmetic
       const int mn = mb + KS;
       T4 nd[PF ? KS : 1][4];
-      if constexpr (PF) {
+      if constexpr (WSEG > 0) if (pre) {
+        // precomputed weights from the stage; the two 16-byte halves are read in
+        // an order that keeps a quarter warp on distinct bank groups
+        const unsigned char* wst = smem + (gi % NS) * STAGE + HIST;
+        const int h0 = (tid >> 2) & 1;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (mb + k < m1 && mb + k < lo) {
+            const double2 p0 = *reinterpret_cast<const double2*>(wst + k * WSEG + tid * 32 + h0 * 16);
+            const double2 p1 = *reinterpret_cast<const double2*>(wst + k * WSEG + tid * 32 + (1 - h0) * 16);
+            const double2 lo2 = h0 ? p1 : p0, hi2 = h0 ? p0 : p1;
+            w[k][0] = lo2.x; w[k][1] = lo2.y; w[k][2] = hi2.x; w[k][3] = hi2.y;
+          } else {
+            w[k][0] = w[k][1] = w[k][2] = w[k][3] = (R)0;
+          }
+        }
+      }
+      if (pre) {
+      } else if constexpr (PF) {
 #pragma unroll
         for (int k = 0; k < KS; ++k)
 #pragma unroll
@@ -354,7 +387,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           }
         }
       }
-      if constexpr (PF) {
+      if constexpr (PF) if (!pre) {
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           if (mn + k < m1 && mn + k < lo) {

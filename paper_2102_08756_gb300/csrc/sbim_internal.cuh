@@ -37,6 +37,8 @@ struct StepArgs {
   const void* table;               // [table_n] (H11, H22, H33, H12) at T = (j-1) h
   const int* lmax;                 // [n_orb_pad] lags kept per orbit (truncation window), or NULL
   const int* tile_lmax;            // [n_orb_pad/128] max of lmax over each tile, or NULL
+  const void* wts;                 // FP64 path: [n_cut][n_orb_pad] precomputed weights
+                                   // (11, 22, 33, 12) as 4 doubles, or NULL
   // state
   void* hist;                      // ring buffer (layout per precision)
   long long* step;                 // device step counter n
@@ -84,6 +86,9 @@ cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
 cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
 cudaError_t launch_rewind(long long* step, cudaStream_t st);
+// FP64 path: out[m][o] = the four convolution weights of orbit o at lag m,
+// m < n_cut (the cubic interpolation of the FP64 table the kernels would do).
+cudaError_t launch_weights64(const StepArgs& a, void* out, cudaStream_t st);
 // *flag = 1 if any of the n values of a or b (b may be NULL) is not finite, else 0.
 cudaError_t launch_nonfinite_check(int precision, const void* a, const void* b, long long n,
                                    int* flag, cudaStream_t st);
