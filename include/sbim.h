@@ -268,6 +268,19 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
 int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta);
 
 /*
+ * sbim_set_conv_tile -- orbit records per CTA of the TMA-staged convolution
+ * (variants 1-3; Section 2.3's per-mode convolution, one thread per record of 4
+ * Fourier-bin members): 64, 128 (the default) or 256, i.e. 256, 512 or 1024
+ * member slots ("modes") per CTA.  A shape's shared memory and threads per SM
+ * stay the same (twice the resident CTAs at 64, half at 256).  SBIM_ERR_ARG
+ * unless the handle's record count (n_slots / 4) is a multiple of it.  The
+ * results equal the 128-record launch's to within float rounding.  May
+ * reallocate the partial sums; on failure the previous setting is kept.
+ * Library utility: the paper has no counterpart.
+ */
+int sbim_set_conv_tile(sbim_handle h, int orbits_per_cta);
+
+/*
  * sbim_set_window -- mode-dependent truncation of the convolution (Section 1 cites
  * the truncation of Lapusta et al. without giving a rule): a window fixed in the
  * dimensionless time T = |k| c_s t, so mode k keeps its lags m with
@@ -388,6 +401,12 @@ int sbim_batch_replay(sbim_batch b);
  * counterpart.
  */
 int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
+
+/* sbim_batch_set_conv_tile -- orbit records per CTA of the batch's convolution
+ * (64, 128 or 256; as sbim_set_conv_tile), keeping the shape and the lags per
+ * item; SBIM_ERR_ARG unless every member's record count is a multiple of it.
+ * Drops a captured graph.  Library utility: the paper has no counterpart. */
+int sbim_batch_set_conv_tile(sbim_batch b, int orbits_per_cta);
 
 /* sbim_batch_member -- the handle of member i (owned by the batch).  Library utility:
  * the paper has no counterpart. */
@@ -572,6 +591,10 @@ int sbim_hybrid_batch_replay(sbim_hybrid_batch b);
  * batch's 2 nb half-spaces; drops a captured graph.  Library utility: the paper has
  * no counterpart. */
 int sbim_hybrid_batch_set_conv_config(sbim_hybrid_batch b, int shape, int lags_per_item);
+/* sbim_hybrid_batch_set_conv_tile -- as sbim_batch_set_conv_tile for the batch's
+ * 2 nb half-spaces; drops a captured graph.  Library utility: the paper has no
+ * counterpart. */
+int sbim_hybrid_batch_set_conv_tile(sbim_hybrid_batch b, int orbits_per_cta);
 int sbim_hybrid_batch_destroy(sbim_hybrid_batch b);
 
 /* sbim_destroy -- free everything the handle owns; NULL is accepted.  Library utility:

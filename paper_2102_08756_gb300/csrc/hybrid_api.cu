@@ -553,6 +553,13 @@ int sbim_hybrid_batch_set_conv_config(sbim_hybrid_batch b, int shape, int lags_p
   return sbim::batch_set_conv_config(b->sb, shape, lags_per_item);
 }
 
+int sbim_hybrid_batch_set_conv_tile(sbim_hybrid_batch b, int orbits_per_cta) {
+  if (!b) return hfail(SBIM_ERR_ARG, "NULL batch");
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  return sbim::batch_set_conv_tile(b->sb, orbits_per_cta);
+}
+
 int sbim_hybrid_batch_replay(sbim_hybrid_batch b) {
   if (!b) return hfail(SBIM_ERR_ARG, "NULL batch");
   if (!b->exec) return hfail(SBIM_ERR_STATE, "no captured step: call sbim_hybrid_batch_capture");

@@ -106,6 +106,7 @@ struct sbim_ctx {
   cudaStream_t stream = nullptr;
   int n_orb = 0, n_orb_pad = 0, lc = 1, nchunks = 1;
   int variant = 1;            // 0: register-prefetch loads, 1-3: TMA-staged history shapes
+  int tile = sbim::kOrbitTile;  // orbits per CTA of the TMA convolution: 64, 128 or 256
   int lags_per_cta = 0;       // 0: automatic
   size_t part_bytes = 0;
   double tab_h = 0;
@@ -281,8 +282,8 @@ int choose_chunks(sbim_ctx& c) {
   if (c.lags_per_cta > 0) {
     c.lc = std::min(c.lags_per_cta, c.n_cut);
   } else {
-    const long long tiles = c.n_orb_pad / sbim::kOrbitTile;
-    const int per_sm = c.variant >= 1 ? sbim::conv_tma_ctas_per_sm(c.prec, c.variant)
+    const long long tiles = c.n_orb_pad / (c.variant >= 1 ? c.tile : sbim::kOrbitTile);
+    const int per_sm = c.variant >= 1 ? sbim::conv_tma_ctas_per_sm(c.prec, c.variant, c.tile)
                                       : (c.prec == SBIM_FP64 ? 1 : 3);
     const long long target = (long long)sms * per_sm * 16;
     long long S = (target + tiles - 1) / tiles;
@@ -389,7 +390,7 @@ int create_impl(sbim_ctx* c) {
   }
 
   if (choose_chunks(*c) != SBIM_OK) return SBIM_ERR_CUDA;
-  if (c->variant >= 1) CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant));
+  if (c->variant >= 1) CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant, c->tile));
 
   // history size
   c->plane_records = (long long)c->n_cut * 3 * c->n_orb_pad;
@@ -671,7 +672,7 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
   if (repeat)
     CU(sbim::launch_repeat_lag0(a, c->prec, st));
   else if (c->variant >= 1)
-    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st));
+    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile));
   else
     CU(sbim::launch_conv(a, c->prec, c->kahan, st));
   if (e) CU(cudaEventRecord(e[2], st));
@@ -769,7 +770,7 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
     sbim::StepArgs a = step_args(c);
     a.uhat = zero_hat;
     if (c->variant >= 1)
-      CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st));
+      CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile));
     else
       CU(sbim::launch_conv(a, c->prec, c->kahan, st));
     CU(cudaStreamWaitEvent(st, c->io_join, 0));
@@ -857,7 +858,7 @@ int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   h->variant = variant;
   h->lags_per_cta = lags_per_cta;
   if (variant >= 1) {
-    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, variant);
+    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, variant, h->tile);
     if (e != cudaSuccess) {
       h->variant = old_v;
       h->lags_per_cta = old_l;
@@ -868,6 +869,32 @@ int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   if (rc == SBIM_OK) rc = alloc_partials(*h);
   if (rc != SBIM_OK) {
     h->variant = old_v; h->lags_per_cta = old_l; h->lc = old_lc; h->nchunks = old_nc;
+    return rc;
+  }
+  return SBIM_OK;
+}
+
+int sbim_set_conv_tile(sbim_handle h, int orbits_per_cta) {
+  if (!h) return fail(SBIM_ERR_ARG, "NULL handle");
+  if (orbits_per_cta != 64 && orbits_per_cta != 128 && orbits_per_cta != 256)
+    return fail(SBIM_ERR_ARG, "orbits per CTA must be 64, 128 or 256");
+  if (h->n_orb_pad % orbits_per_cta != 0)
+    return fail(SBIM_ERR_ARG, "the handle's %d orbit records are not a multiple of %d",
+                h->n_orb_pad, orbits_per_cta);
+  h->can_repeat = false;
+  const int old_t = h->tile, old_lc = h->lc, old_nc = h->nchunks;
+  h->tile = orbits_per_cta;
+  if (h->variant >= 1) {
+    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, h->variant, h->tile);
+    if (e != cudaSuccess) {
+      h->tile = old_t;
+      return fail(SBIM_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    }
+  }
+  int rc = choose_chunks(*h);
+  if (rc == SBIM_OK) rc = alloc_partials(*h);
+  if (rc != SBIM_OK) {
+    h->tile = old_t; h->lc = old_lc; h->nchunks = old_nc;
     return rc;
   }
   return SBIM_OK;

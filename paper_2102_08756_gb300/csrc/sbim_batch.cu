@@ -15,6 +15,8 @@
 
 struct sbim_batch_ctx {
   int nb = 0, prec = SBIM_FP32, kahan = 1, shape = 2;
+  int tile = sbim::kOrbitTile;   // orbits per CTA of the batched convolution
+  int lags = 0;                  // lags per work item last configured
   bool per_item = false;    // one CTA per work item instead of persistent CTAs
   bool owns = true;
   cudaStream_t stream = nullptr;
@@ -110,15 +112,15 @@ int configure(sbim_batch_ctx* b, int shape, int lags) {
     const int rc = sbim_set_conv_config(b->h[i], shape, lags);
     if (rc != SBIM_OK) return rc;
   }
-  BCU(sbim::prepare_conv_tma(b->prec, b->kahan, shape));
+  BCU(sbim::prepare_conv_tma(b->prec, b->kahan, shape, b->tile));
   b->shape = shape;
+  b->lags = lags;
   std::vector<sbim::StepArgs> args(b->nb);
   std::vector<int> items(b->nb + 1, 0), tiles(b->nb + 1, 0);
   for (int i = 0; i < b->nb; ++i) {
     args[i] = sbim::handle_step_args(b->h[i]);
-    const int t = args[i].n_orb_pad / sbim::kOrbitTile;
-    tiles[i + 1] = tiles[i] + t;
-    items[i + 1] = items[i] + t * args[i].nchunks;
+    tiles[i + 1] = tiles[i] + args[i].n_orb_pad / sbim::kOrbitTile;   // assembly tiles
+    items[i + 1] = items[i] + args[i].n_orb_pad / b->tile * args[i].nchunks;
   }
   b->total_items = items[b->nb];
   b->total_tiles = tiles[b->nb];
@@ -136,7 +138,7 @@ int configure(sbim_batch_ctx* b, int shape, int lags) {
   int dev = 0, sms = 148;
   BCU(cudaGetDevice(&dev));
   BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape);
+  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape, b->tile);
   return SBIM_OK;
 }
 
@@ -187,7 +189,7 @@ int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void*
   bl.ctas = b->ctas;
   bl.items = b->per_item ? b->total_items : 0;
   const sbim::StepArgs a0 = sbim::handle_step_args(b->h[0]);
-  BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl));
+  BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl, b->tile));
   BCU(sbim::launch_assemble_batch(bl, b->total_tiles, b->prec, b->kahan, b->stream));
   rc = fork(b);
   for (int i = 0; i < b->nb && rc == SBIM_OK; ++i) {
@@ -225,6 +227,7 @@ int batch_join(sbim_batch b) { return join(b); }
 int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
   return sbim_batch_set_conv_config(b, shape, lags_per_item);
 }
+int batch_set_conv_tile(sbim_batch b, int tile) { return sbim_batch_set_conv_tile(b, tile); }
 void batch_advance(sbim_batch b) {
   for (sbim_handle x : b->h) handle_advance(x);
 }
@@ -310,6 +313,24 @@ int sbim_batch_set_conv_config(sbim_batch b, int shape, int lags_per_item) {
   drop_graph(b);
   b->per_item = shape > 3;
   return configure(b, shape > 3 ? shape - 3 : shape, lags_per_item ? lags_per_item : kBatchLags);
+}
+
+int sbim_batch_set_conv_tile(sbim_batch b, int orbits_per_cta) {
+  if (!b) return bfail(SBIM_ERR_ARG, "NULL batch");
+  if (orbits_per_cta != 64 && orbits_per_cta != 128 && orbits_per_cta != 256)
+    return bfail(SBIM_ERR_ARG, "orbits per CTA must be 64, 128 or 256");
+  for (int i = 0; i < b->nb; ++i) {
+    const int n = sbim::handle_step_args(b->h[i]).n_orb_pad;
+    if (n % orbits_per_cta != 0)
+      return bfail(SBIM_ERR_ARG, "member %d has %d orbit records, not a multiple of %d", i, n,
+                   orbits_per_cta);
+  }
+  drop_graph(b);
+  const int old = b->tile;
+  b->tile = orbits_per_cta;
+  const int rc = configure(b, b->shape, b->lags);
+  if (rc != SBIM_OK) b->tile = old;
+  return rc;
 }
 
 int sbim_batch_member(sbim_batch b, int i, sbim_handle* h) {

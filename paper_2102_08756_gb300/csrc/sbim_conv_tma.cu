@@ -30,38 +30,38 @@ cudaError_t launch_wait_selftest(int* err, cudaStream_t st) {
 }
 
 cudaError_t launch_conv_tma_f32(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep);
+                                 const BatchLaunch* batch, bool prep, int tile);
 cudaError_t launch_conv_tma_bf16x2(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep);
+                                 const BatchLaunch* batch, bool prep, int tile);
 cudaError_t launch_conv_tma_bf16(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep);
+                                 const BatchLaunch* batch, bool prep, int tile);
 cudaError_t launch_conv_tma_f64(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep);
+                                 const BatchLaunch* batch, bool prep, int tile);
 
 static cudaError_t dispatch(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t st, const BatchLaunch* batch, bool prep) {
+                            cudaStream_t st, const BatchLaunch* batch, bool prep, int tile) {
   switch (precision) {
-    case SBIM_FP64: return launch_conv_tma_f64(a, 0, shape, st, batch, prep);
-    case SBIM_FP32: return launch_conv_tma_f32(a, kahan, shape, st, batch, prep);
-    case SBIM_BF16X2: return launch_conv_tma_bf16x2(a, kahan, shape, st, batch, prep);
-    case SBIM_BF16: return launch_conv_tma_bf16(a, kahan, shape, st, batch, prep);
+    case SBIM_FP64: return launch_conv_tma_f64(a, 0, shape, st, batch, prep, tile);
+    case SBIM_FP32: return launch_conv_tma_f32(a, kahan, shape, st, batch, prep, tile);
+    case SBIM_BF16X2: return launch_conv_tma_bf16x2(a, kahan, shape, st, batch, prep, tile);
+    case SBIM_BF16: return launch_conv_tma_bf16(a, kahan, shape, st, batch, prep, tile);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t st, const BatchLaunch* batch) {
-  return dispatch(a, precision, kahan, shape, st, batch, false);
+                            cudaStream_t st, const BatchLaunch* batch, int tile) {
+  return dispatch(a, precision, kahan, shape, st, batch, false, tile);
 }
 
-cudaError_t prepare_conv_tma(int precision, int kahan, int shape) {
+cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile) {
   const StepArgs none{};
-  return dispatch(none, precision, kahan, shape, nullptr, nullptr, true);
+  return dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile);
 }
 
-int conv_tma_ctas_per_sm(int precision, int shape) {
-  if (precision == SBIM_FP64) return 2;
-  return shape == 2 ? 3 : 2;
+int conv_tma_ctas_per_sm(int precision, int shape, int tile) {
+  const int minb = (precision == SBIM_FP64) ? 2 : (shape == 2 ? 3 : 2);
+  return tma::minb_for_tile(minb, tile);
 }
 
 }  // namespace sbim

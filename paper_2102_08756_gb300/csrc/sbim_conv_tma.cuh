@@ -2,9 +2,10 @@
 // bulk copies (Section 2.3, spectral evaluation of s_i: the per-mode truncated
 // time convolution, step A4).
 //
-// One CTA = one tile of 128 orbits (one thread per orbit) and one chunk of lags.
-// For every lag the tile's history lives in 3 contiguous segments of global
-// memory (one per component, 128 records each), so an elected thread stages a
+// One CTA = one tile of TILE orbits (one thread per orbit; TILE = 64, 128 or
+// 256, the handle's "modes per CTA") and one chunk of lags.  For every lag the
+// tile's history lives in 3 contiguous segments of global memory (one per
+// component, TILE records each), so an elected thread stages a
 // pipeline stage of KS lags with 3 KS cp.async.bulk copies completing on an
 // mbarrier, NS stages deep; the bytes in flight cost no registers.  Threads read
 // their own 16-byte chunks from the staged segments with a per-quarter-warp
@@ -97,20 +98,26 @@ template <bool LO> struct PrefetchNodes<dev::StoreBF16<LO>, 1> {
   static constexpr bool value = false;
 };
 
-template <class S>
-__host__ __device__ constexpr int seg_bytes() { return kOrbitTile * S::kRecBytes; }
+template <class S, int TILE>
+__host__ __device__ constexpr int seg_bytes() { return TILE * S::kRecBytes; }
 // FP64 history: a stage also holds each lag's precomputed weights (4 doubles per
 // orbit) when the handle keeps them (StepArgs::wts); the float paths interpolate.
-template <class S>
+template <class S, int TILE>
 __host__ __device__ constexpr int wseg_bytes() {
-  return std::is_same<S, dev::StoreF64>::value ? kOrbitTile * 32 : 0;
+  return std::is_same<S, dev::StoreF64>::value ? TILE * 32 : 0;
 }
-template <class S, int KS>
+template <class S, int KS, int TILE>
 __host__ __device__ constexpr int stage_bytes() {
-  return KS * (3 * S::kPlanes * seg_bytes<S>() + wseg_bytes<S>());
+  return KS * (3 * S::kPlanes * seg_bytes<S, TILE>() + wseg_bytes<S, TILE>());
 }
-template <class S, int NS, int KS>
-__host__ __device__ constexpr int smem_bytes() { return NS * stage_bytes<S, KS>(); }
+template <class S, int NS, int KS, int TILE>
+__host__ __device__ constexpr int smem_bytes() { return NS * stage_bytes<S, KS, TILE>(); }
+
+// Resident CTAs per SM of a pipeline shape (sized for 128-orbit tiles) at
+// another tile: the same shared memory and threads per SM.
+__host__ __device__ constexpr int minb_for_tile(int minb, int tile) {
+  return tile == 64 ? 2 * minb : (tile == 256 ? (minb / 2 > 0 ? minb / 2 : 1) : minb);
+}
 
 // The four table nodes of one lag, and their cubic Lagrange combination (the
 // two halves of dev::lag_weights, split so the loads can be issued early).
@@ -145,26 +152,34 @@ __device__ __forceinline__ void interp_nodes(const T4 nd[4], unsigned long long 
 // over from item to item through the running stage count `gstage` (stage s of
 // this item is global stage gstage + s: buffer (gstage + s) % NS, parity
 // ((gstage + s) / NS) & 1).  Returns false if a bounded wait gave up.
-template <class S, int KAHAN, int NS, int KS>
+template <class S, int KAHAN, int NS, int KS, int TILE>
 __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int chunk,
                                               unsigned char* smem, unsigned long long* full,
                                               unsigned& gstage) {
   using R = typename S::real;
   using C = typename S::cplx;
   using T4 = typename S::tab4;
-  constexpr int SEG = seg_bytes<S>();
-  constexpr int WSEG = wseg_bytes<S>();
+  constexpr int SEG = seg_bytes<S, TILE>();
+  constexpr int WSEG = wseg_bytes<S, TILE>();
   constexpr int HIST = KS * 3 * S::kPlanes * SEG;   // history part of a stage
-  constexpr int STAGE = stage_bytes<S, KS>();
+  constexpr int STAGE = stage_bytes<S, KS, TILE>();
   constexpr int MPC = S::kChunkMembers, NCH = S::kChunks;
 
   const int tid = threadIdx.x;
-  const int tile0 = tile * kOrbitTile;
+  const int tile0 = tile * TILE;
   const int o = tile0 + tid;
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
   const int m0 = chunk * a.lc;
-  const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[tile]) : n_valid;
+  // the truncation window's lag limit is kept per 128-orbit tile
+  int m_end = n_valid;
+  if (a.tile_lmax) {
+    int lim = 0;
+#pragma unroll
+    for (int t = 0; t < (TILE + kOrbitTile - 1) / kOrbitTile; ++t)
+      lim = max(lim, a.tile_lmax[tile0 / kOrbitTile + t]);
+    m_end = min(n_valid, lim);
+  }
   if (m0 >= m_end) return true;   // uniform over the CTA
   const int m1 = min(m0 + a.lc, m_end);
   const int lo = a.lmax ? a.lmax[o] : 0x7fffffff;   // this orbit's truncation
@@ -434,13 +449,13 @@ __device__ __forceinline__ void init_barriers(unsigned long long* full) {
 }
 
 // One CTA per (orbit tile, lag chunk) of one update.
-template <class S, int KAHAN, int NS, int KS, int MINB>
-__global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepArgs a) {
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+__global__ void __launch_bounds__(TILE, MINB) conv_tma_kernel(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full[NS];
   init_barriers<NS>(full);
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, TILE>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
 }
 
 // Persistent CTAs over the (update, tile, chunk) items of a batch of updates
@@ -448,8 +463,8 @@ __global__ void __launch_bounds__(kOrbitTile, MINB) conv_tma_kernel(const StepAr
 // order (item_prefix[s] .. item_prefix[s+1]-1 belong to update s, tile-major
 // within each lag chunk).  Every item writes its own partial sums, so the
 // result does not depend on which CTA ran it.
-template <class S, int KAHAN, int NS, int KS, int MINB>
-__global__ void __launch_bounds__(kOrbitTile, MINB)
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+__global__ void __launch_bounds__(TILE, MINB)
 conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
                       int nb, int* counter) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -468,7 +483,7 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
         int s = 0;
         while (s + 1 < nb && item_prefix[s + 1] <= it) ++s;
         s_args = args[s];
-        const int tiles = s_args.n_orb_pad / kOrbitTile;
+        const int tiles = s_args.n_orb_pad / TILE;
         const int local = it - item_prefix[s];
         s_tile = local % tiles;
         s_chunk = local / tiles;
@@ -476,7 +491,7 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
     }
     __syncthreads();
     if (s_item >= total) break;
-    if (!conv_tma_item<S, KAHAN, NS, KS>(s_args, s_tile, s_chunk, smem, full, gstage)) return;
+    if (!conv_tma_item<S, KAHAN, NS, KS, TILE>(s_args, s_tile, s_chunk, smem, full, gstage)) return;
   }
 }
 
@@ -484,8 +499,8 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
 // scheduler hands the items out; no work counter, and no barrier phases carried
 // from item to item, so its register needs are those of the single-update
 // kernel).  Same item order as the persistent kernel.
-template <class S, int KAHAN, int NS, int KS, int MINB>
-__global__ void __launch_bounds__(kOrbitTile, MINB)
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+__global__ void __launch_bounds__(TILE, MINB)
 conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
                       int nb) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -497,31 +512,31 @@ conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__
     int s = 0;
     while (s + 1 < nb && item_prefix[s + 1] <= it) ++s;
     s_args = args[s];
-    const int tiles = s_args.n_orb_pad / kOrbitTile;
+    const int tiles = s_args.n_orb_pad / TILE;
     const int local = it - item_prefix[s];
     s_tile = local % tiles;
     s_chunk = local / tiles;
   }
   init_barriers<NS>(full);   // its __syncthreads publishes the item too
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS>(s_args, s_tile, s_chunk, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, TILE>(s_args, s_tile, s_chunk, smem, full, gstage);
 }
 
 // Launch one instantiation (sets the dynamic shared-memory attribute once).
 // With `batch` set, launches over the batch's items instead: one CTA per item
 // when `batch->items` > 0, else the persistent kernel on `batch->ctas` CTAs.
-template <class S, int KAHAN, int NS, int KS, int MINB>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
 cudaError_t prepare_shape() {
   static bool attr_set = false;
-  constexpr int bytes = smem_bytes<S, NS, KS>();
+  constexpr int bytes = smem_bytes<S, NS, KS, TILE>();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB>,
+      e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv_tma_items_kernel<S, KAHAN, NS, KS, MINB>,
+      e = cudaFuncSetAttribute(conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -530,23 +545,42 @@ cudaError_t prepare_shape() {
 }
 
 // With `batch` null and `prepare_only` set, only sets the kernels' attributes.
-template <class S, int KAHAN, int NS, int KS, int MINB>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
 cudaError_t launch_shape(const StepArgs& a, cudaStream_t st, const BatchLaunch* batch = nullptr,
                          bool prepare_only = false) {
-  constexpr int bytes = smem_bytes<S, NS, KS>();
-  const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB>();
+  constexpr int bytes = smem_bytes<S, NS, KS, TILE>();
+  const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB, TILE>();
   if (pe != cudaSuccess || prepare_only) return pe;
   if (batch && batch->items > 0) {
-    conv_tma_items_kernel<S, KAHAN, NS, KS, MINB><<<batch->items, kOrbitTile, bytes, st>>>(
+    conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE><<<batch->items, TILE, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb);
   } else if (batch) {
-    conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB><<<batch->ctas, kOrbitTile, bytes, st>>>(
+    conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE><<<batch->ctas, TILE, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb, batch->counter);
   } else {
-    const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
-    conv_tma_kernel<S, KAHAN, NS, KS, MINB><<<grid, kOrbitTile, bytes, st>>>(a);
+    if (a.n_orb_pad % TILE != 0) return cudaErrorInvalidValue;
+    const dim3 grid(a.n_orb_pad / TILE, a.nchunks);
+    conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE><<<grid, TILE, bytes, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+// A pipeline shape (sized for 128-orbit tiles: MINB resident CTAs per SM) at the
+// orbit tile `tile`.
+template <class S, int KAHAN, int NS, int KS, int MINB>
+cudaError_t launch_tiles(int tile, const StepArgs& a, cudaStream_t st, const BatchLaunch* batch,
+                         bool prepare_only) {
+  switch (tile) {
+    case 64:
+      return launch_shape<S, KAHAN, NS, KS, minb_for_tile(MINB, 64), 64>(a, st, batch, prepare_only);
+    case 128:
+      return launch_shape<S, KAHAN, NS, KS, MINB, 128>(a, st, batch, prepare_only);
+    case 256:
+      return launch_shape<S, KAHAN, NS, KS, minb_for_tile(MINB, 256), 256>(a, st, batch,
+                                                                          prepare_only);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace tma

@@ -8,20 +8,20 @@ namespace sbim {
 
 template <int KAHAN>
 static cudaError_t shapes_bf16x2(const StepArgs& a, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep) {
+                                 const BatchLaunch* batch, bool prep, int tile) {
   using S = dev::StoreBF16<true>;
   switch (shape) {
-    case 1: return tma::launch_shape<S, KAHAN, 4, 2, 2>(a, st, batch, prep);
-    case 2: return tma::launch_shape<S, KAHAN, 3, 2, 3>(a, st, batch, prep);
-    case 3: return tma::launch_shape<S, KAHAN, 2, 4, 2>(a, st, batch, prep);
+    case 1: return tma::launch_tiles<S, KAHAN, 4, 2, 2>(tile, a, st, batch, prep);
+    case 2: return tma::launch_tiles<S, KAHAN, 3, 2, 3>(tile, a, st, batch, prep);
+    case 3: return tma::launch_tiles<S, KAHAN, 2, 4, 2>(tile, a, st, batch, prep);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_conv_tma_bf16x2(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep) {
-  return kahan ? shapes_bf16x2<1>(a, shape, st, batch, prep)
-               : shapes_bf16x2<0>(a, shape, st, batch, prep);
+                                 const BatchLaunch* batch, bool prep, int tile) {
+  return kahan ? shapes_bf16x2<1>(a, shape, st, batch, prep, tile)
+               : shapes_bf16x2<0>(a, shape, st, batch, prep, tile);
 }
 
 }  // namespace sbim

@@ -23,7 +23,8 @@ namespace sbim {
 
 constexpr int kMembers = 4;      // members per orbit
 constexpr int kFields = 10;      // real accumulators per member: 5 complex sums
-constexpr int kOrbitTile = 128;  // orbits per CTA of the convolution kernel
+constexpr int kOrbitTile = 128;  // orbits per CTA of the assembly and of the default convolution
+                                 // (the TMA convolution also runs 64 or 256: "modes per CTA")
 
 // Everything the per-step kernels read; device pointers unless noted.
 struct StepArgs {
@@ -75,13 +76,15 @@ cudaError_t launch_assemble_batch(const BatchLaunch& b, int total_tiles, int pre
 // History convolution with TMA bulk-copy staging of the history slots in shared
 // memory (same inputs and outputs as launch_conv).  ctas_per_sm reports the
 // residency the launch is sized for.
-// shape 1..3 selects the pipeline (stages, lags per stage, CTAs per SM).
+// shape 1..3 selects the pipeline (stages, lags per stage, CTAs per SM); tile the
+// orbits per CTA (64, 128 or 256; n_orb_pad must be a multiple of it).
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t s, const BatchLaunch* batch = nullptr);
-int conv_tma_ctas_per_sm(int precision, int shape);
+                            cudaStream_t s, const BatchLaunch* batch = nullptr,
+                            int tile = kOrbitTile);
+int conv_tma_ctas_per_sm(int precision, int shape, int tile = kOrbitTile);
 // Set the shared-memory attributes of a shape's kernels (done before any launch,
 // so that launches can be captured in a CUDA graph).
-cudaError_t prepare_conv_tma(int precision, int kahan, int shape);
+cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile = kOrbitTile);
 // One CTA whose bounded mbarrier wait can never complete (sbim_selftest_wait_timeout).
 cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);
@@ -122,6 +125,7 @@ int handle_shape(sbim_handle h, int* precision, int* kahan, int* variant, void**
 // Batch over existing handles (not owned); enqueue one step / advance the counters.
 int batch_from_handles(sbim_batch* out, const sbim_handle* hs, int n);
 int batch_set_conv_config(sbim_batch b, int shape, int lags_per_item);
+int batch_set_conv_tile(sbim_batch b, int tile);
 // Fork / join of the batch's side streams around per-member stages: after
 // batch_fork, work on batch_side(b, i) follows everything enqueued on the
 // batch's stream; batch_join makes the batch's stream wait for all of it.

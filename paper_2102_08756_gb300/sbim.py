@@ -52,6 +52,9 @@ def lib():
     L.sbim_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.sbim_set_profiling.argtypes = [vp, i]
     L.sbim_set_check_finite.argtypes = [vp, i]
+    L.sbim_set_conv_tile.argtypes = [vp, i]
+    L.sbim_batch_set_conv_tile.argtypes = [vp, i]
+    L.sbim_hybrid_batch_set_conv_tile.argtypes = [vp, i]
     L.sbim_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ll)]
     L.sbim_set_conv_config.argtypes = [vp, i, i]
     L.sbim_set_window.argtypes = [vp, d]
@@ -96,7 +99,8 @@ def lib():
     for name in ("sbim_create", "sbim_step", "sbim_step_host", "sbim_step_adjoint",
                  "sbim_set_far_field",
                  "sbim_reset", "sbim_get_step", "sbim_get_info", "sbim_plan", "sbim_set_profiling",
-                 "sbim_set_check_finite",
+                 "sbim_set_check_finite", "sbim_set_conv_tile", "sbim_batch_set_conv_tile",
+                 "sbim_hybrid_batch_set_conv_tile",
                  "sbim_stage_times", "sbim_set_conv_config", "sbim_check_device", "sbim_set_window",
                  "sbim_spectral_response_noalloc", "sbim_destroy", "sbim_hybrid_create",
                  "sbim_hybrid_set_fault", "sbim_hybrid_set_state", "sbim_hybrid_get_state",
@@ -199,6 +203,18 @@ def sbim_set_profiling(h, enable):
 
 def sbim_set_check_finite(h, enable):
     _check(lib().sbim_set_check_finite(h, int(enable)))
+
+
+def sbim_set_conv_tile(h, orbits_per_cta):
+    _check(lib().sbim_set_conv_tile(h, int(orbits_per_cta)))
+
+
+def sbim_batch_set_conv_tile(b, orbits_per_cta):
+    _check(lib().sbim_batch_set_conv_tile(b, int(orbits_per_cta)))
+
+
+def sbim_hybrid_batch_set_conv_tile(b, orbits_per_cta):
+    _check(lib().sbim_hybrid_batch_set_conv_tile(b, int(orbits_per_cta)))
 
 
 def sbim_stage_times(h):
@@ -499,6 +515,9 @@ class SBIM:
 
     def set_check_finite(self, enable=True):
         sbim_set_check_finite(self.h, enable)
+
+    def set_conv_tile(self, orbits_per_cta):
+        sbim_set_conv_tile(self.h, orbits_per_cta)
 
     def stage_times(self):
         return sbim_stage_times(self.h)

@@ -44,20 +44,26 @@ def _fields(hist, m):
     return u, v
 
 
-@pytest.mark.parametrize("shape,lags", [(None, None), (3, 256), (2, 64), (5, 64), (4, 1024)])
-def test_batch_equals_members_stepped_alone(shape, lags):
+@pytest.mark.parametrize("shape,lags,tile", [(None, None, 128), (3, 256, 128), (2, 64, 128),
+                                             (5, 64, 128), (4, 1024, 128), (None, None, 64),
+                                             (2, 64, 64), (4, 64, 64)])
+def test_batch_equals_members_stepped_alone(shape, lags, tile):
     """Default launch (one CTA per 1024-lag item, pipeline shape 2) and others set with
-    sbim_batch_set_conv_config, persistent (1-3) and one CTA per item (4-6)."""
+    sbim_batch_set_conv_config, persistent (1-3) and one CTA per item (4-6), at 128
+    and 64 orbit records per CTA (sbim_batch_set_conv_tile)."""
     from paper_2102_08756_gb300.sbim import SBIM
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         B, b, hist, dt = _setup(stream)
         if shape is not None:
             B.sbim_batch_set_conv_config(b, shape, lags)
+        if tile != 128:
+            B.sbim_batch_set_conv_tile(b, tile)
         alone = []
         for (a, c, n_cut, side) in MEMBERS:
             h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "fp32", True,
                      stream=stream)
+            h.set_conv_tile(tile)
             if shape is None:
                 h.set_conv_config(2, 1024)
             else:

@@ -49,6 +49,10 @@ def test_dc_gradient_matches_oracle(precision, tol):
     (g,) = torch.autograd.grad(J, dc)
     assert_finite(out, "boundary tractions")
     assert_finite(g, "dJ/dDc")
+    print(f"\nGRADIENT-REPORT {precision}: dJ/dDc {float(g):.6e} oracle {ref.sum():.6e} "
+          f"relative error {abs(float(g) - ref.sum()) / abs(ref.sum()):.3e}; traction error "
+          f"{np.abs(out.detach().double().cpu().numpy() - taus).max() / np.abs(taus).max():.3e} "
+          f"of the peak")
     np.testing.assert_allclose(out.detach().double().cpu().numpy(), taus, rtol=0,
                                atol=(1e-7 if precision == "fp64" else 5e-3) * np.abs(taus).max())
     assert abs(float(g) - ref.sum()) < tol * abs(ref.sum()), (float(g), ref.sum())

@@ -52,14 +52,20 @@ def test_rupture_matches_oracle(precision, tol, symmetric, n1, n3, n_cut):
     g = _solver(n1, n3, n_cut, fl, precision, symmetric)
     worst = {"rate": Worst(), "slip": Worst(), "traction": Worst()}
     peak = 0.0
+    rates, refs = [], []
     for _ in range(steps):
         o.step()
         g.step()
         slip, rate, trac = (x.double().cpu().numpy() for x in g.fault_fields())
+        rates.append(rate)
+        refs.append(o.slip_rate.copy())
         for name, got, ref in (("rate", rate, o.slip_rate), ("slip", slip, o.slip),
                                ("traction", trac, o.fault_traction)):
             worst[name].update(max_abs_rel(got, ref, max(np.abs(ref).max(), 1e-30)))
         peak = max(peak, np.abs(o.slip_rate).max())
+    from tests.test_gpu_hybrid import regime_report
+    print("\n" + regime_report(f"RUPTURE-REPORT sbim {precision} sym={symmetric} {n1}x{n3}",
+                                rates, refs))
     assert peak > 1.0, peak                         # the rupture runs
     assert all(w.value < tol for w in worst.values()), worst
     u, v = (x.double().cpu().numpy() for x in g.get_state())

@@ -23,6 +23,24 @@ def built():
 rel = rel_l2_field
 
 
+def regime_report(title, rates, refs, thr=1e-3):
+    """Where a lower-precision rupture departs from the FP64 one: the nodes that
+    slip (|slip rate| > thr m/s) at some step in one run but not the other, and
+    the slip-rate error inside and outside that set (max over steps, relative to
+    the FP64 peak)."""
+    rates, refs = np.array(rates), np.array(refs)
+    mag = lambda x: np.sqrt((x ** 2).sum(axis=1))           # noqa: E731  (steps, n3, n1)
+    a, b = mag(rates) > thr, mag(refs) > thr
+    switch = (a != b).any(axis=0)
+    peak = np.abs(refs).max()
+    d = np.abs(rates - refs).max(axis=(0, 1))
+    inside = d[switch].max() / peak if switch.any() else 0.0
+    outside = d[~switch].max() / peak if (~switch).any() else 0.0
+    return (f"{title}: {int(switch.sum())} of {switch.size} nodes change regime at another step; "
+            f"slip-rate error inside {inside:.3e}, outside {outside:.3e}, overall "
+            f"{d.max() / peak:.3e} of the peak {peak:.3f} m/s")
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
 @pytest.mark.parametrize("fault,boundaries", [(False, True), (True, True), (True, False)])
 def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
@@ -47,6 +65,8 @@ def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
         o.step()
         g.step()
     u, v, a = (x.double().cpu().numpy() for x in g.get_state())
+    print(f"\nSLAB-REPORT {precision} fault={fault} sbim={boundaries}: relative L2 error "
+          f"u {rel(u, o.u):.3e} v {rel(v, o.v):.3e} a {rel(a, o.a):.3e}")
     assert rel(u, o.u) < tol
     assert rel(v, o.v) < tol * 10
     assert rel(a, o.a) < tol * 10
@@ -76,6 +96,7 @@ def test_rupture_matches_oracle(precision, tol):
     g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, steps + 1, precision, True, True)
     g.set_fault(mu_s, tau0, 0.525, 0.02, 120e6)
     worst, peak = Worst(), 0.0
+    rates, refs = [], []
     for _ in range(steps):
         o.step()
         g.step()
@@ -83,8 +104,11 @@ def test_rupture_matches_oracle(precision, tol):
         assert_finite(slip, "slip")
         assert_finite(trac, "traction")
         peak = max(peak, np.abs(o.slip_rate).max())
+        rates.append(rate)
+        refs.append(o.slip_rate.copy())
         if np.linalg.norm(o.slip_rate) > 0:
             worst.update(rel(rate, o.slip_rate))
+    print("\n" + regime_report(f"RUPTURE-REPORT hybrid {precision}", rates, refs))
     assert peak > 1.0
     assert worst.value < tol, worst
     g.close()

@@ -32,7 +32,7 @@ def built():
 
 
 def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
-               spectrum="band", dt=None, tau_inf=None, variant=1):
+               spectrum="band", dt=None, tau_inf=None, variant=1, tile=128, window=0.0):
     from paper_2102_08756_gb300.sbim import SBIM
     dt = dt or 0.3 * (L1 / n1) / CP
     hist = separable_history(n1, n3, L1, L3, steps, dt, CS, seed=seed, spectrum=spectrum)
@@ -41,10 +41,13 @@ def run_parity(n1, n3, L1, L3, n_cut, side, steps, precision, kahan, seed=0,
     g_tau = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
     g_s = SBIM(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, precision, kahan)
     o_tau = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side,
-                       tau_inf=tau_inf if tau_inf is not None else (0, 0, 0))
-    o_s = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side)
-    g_tau.set_conv_config(variant)
-    g_s.set_conv_config(variant)
+                       tau_inf=tau_inf if tau_inf is not None else (0, 0, 0), window=window)
+    o_s = SBIMOracle(n1, n3, L1, L3, CS, CP, RHO, dt, n_cut, side, window=window)
+    for g in (g_tau, g_s):
+        g.set_conv_tile(tile)
+        g.set_conv_config(variant)
+        if window > 0:
+            g.set_window(window)
     if tau_inf is not None:
         g_tau.set_far_field(tau_inf)
     err_s, err_t = Worst(), Worst()
@@ -110,6 +113,39 @@ def test_small_configuration(precision, kahan):
                         precision, kahan, seed=1001, dt=c["dt"])
     assert es < TOL[precision], es
     assert et < TOL[precision], et
+
+
+@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("bf16x2", 1), ("bf16", 0)])
+@pytest.mark.parametrize("tile", [64, 256])
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_orbit_tiles_match_oracle(precision, kahan, tile, variant):
+    """64 and 256 orbit records per CTA (the modes-per-CTA tile) on a square and
+    a rectangular grid whose record counts they divide (256 and 768 records),
+    with ring wrap-around, both half-spaces and a truncation window."""
+    for (n1, n3, L1, L3), side, n_cut, window in (((32, 32, 3200.0, 3200.0), 1, 13, 0.0),
+                                                  ((64, 48, 6400.0, 4800.0), -1, 21, 0.0),
+                                                  ((64, 48, 6400.0, 4800.0), 1, 30, 7.3)):
+        es, et = run_parity(n1, n3, L1, L3, n_cut, side, n_cut + 7, precision, kahan,
+                            seed=tile + n1 + variant, spectrum="k2", variant=variant, tile=tile,
+                            window=window)
+        assert es < TOL[precision], (n1, n3, es)
+        assert et < TOL[precision], (n1, n3, et)
+
+
+def test_orbit_tile_must_divide_the_records():
+    from paper_2102_08756_gb300.sbim import SBIM, SBIMError
+    g = SBIM(48, 32, 4800.0, 3200.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)   # 384 records
+    assert g.info()["n_slots"] == 4 * 384
+    with pytest.raises(SBIMError) as e:
+        g.set_conv_tile(256)
+    assert e.value.code == -1
+    with pytest.raises(SBIMError):
+        g.set_conv_tile(96)
+    g.set_conv_tile(64)
+    z = torch.zeros((3, 32, 48), device="cuda")
+    g.step(z, z)
+    g.check()
+    g.close()
 
 
 def test_far_field_and_uniform_mode():
