@@ -47,6 +47,7 @@ from paper_2102_08756_gb300.synth import config_large, separable_history  # noqa
 MACS_PER_PAIR = 5
 DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 2, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
 # full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
 NCU_TRAFFIC = {"conv_src_sha1": "2441d01ed0673ce4b30497592b19f36e58a35381", "bytes_per_launch": 52.159e9 + 183.25e6}
@@ -536,6 +537,17 @@ def run_native(args):
     alg_bytes = (pairs + modes) * bpp
     achieved = alg_bytes / (conv_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    # the FP64 history is bound by the FP64 pipe: 10 real FMAs (20 flops) per
+    # (mode, lag) pair against GB300's FP64 rate (152 SMs x 2 DFMA/clk x 2 flops
+    # x 2.07 GHz = 1.259 TFLOP/s, nominal)
+    alu = None
+    if prec == "fp64":
+        flops = pairs * 20
+        alu = {"bound": "alu", "achieved": flops / (conv_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+               "unit": "TFLOP/s", "frac": flops / (conv_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+               "traffic": None, "kernel": "conv_tma_kernel", "peak_kind": "nominal (unit count x clock)",
+               "algorithmic_flops_per_launch": flops, "launch_ms": conv_ms,
+               "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
     traffic = None
     if NCU_TRAFFIC["conv_src_sha1"] == conv_src_sha1() and prec == "fp32" and n1 == 1024 \
             and args.variant in (-1, 2) and not args.lags_per_cta and args.window <= 0 \
@@ -589,11 +601,11 @@ def run_native(args):
                    "modes": modes, "history_bytes": hist_bytes,
                    "l2": "inputs larger than L2 (history ring buffer >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "conv_tma_kernel" if (args.variant != 0) else "conv_kernel",
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": conv_ms},
+        "roofline": alu or {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic,
+                            "kernel": "conv_tma_kernel" if (args.variant != 0) else "conv_kernel",
+                            "peak_kind": peak_kind,
+                            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": conv_ms},
         "stage_ms_per_step": {k: v / nprof for k, v in stage.items()},
         "hbm_gbs_step": alg_bytes / (ms_step * 1e-3) / 1e9,
         "cpu_baseline": cpu,
