@@ -197,8 +197,13 @@ int sbim_load(sbim_handle h, const void* buf, size_t bytes);
  * sbim_get_info -- sizes of the handle's spectral work, for throughput
  * accounting.  Any pointer may be NULL.
  *   n_modes     half-spectrum Fourier bins, n3 (n1/2 + 1)
- *   n_slots     storage slots per history step: equal-|k| groups x 4 members
- *               (Nyquist bins count twice or four times, padding included)
+ *   n_slots     storage slots per history step: records of 4 member slots
+ *               (Nyquist bins count twice, the corner four times; padding
+ *               included).  A record is two halves of 2 slots, each half's
+ *               members sharing |k|; whole-record layouts give a record one
+ *               class of equal |k|, half-record layouts (used when whole records
+ *               would pad the history by more than 3 %, as on rectangular
+ *               planes) pair the halves of two classes
  *   hist_bytes  bytes of the history ring buffer
  *   table_nodes entries of the interpolated kernel table
  * Library utility: the paper has no counterpart.
@@ -210,8 +215,9 @@ int sbim_get_info(sbim_handle h, long long* n_modes, long long* n_slots,
  * sbim_plan -- the spectral layout sbim_create builds for a grid, computed on
  * the host without touching the device, so that device memory can be budgeted
  * before any handle exists.  Outputs as sbim_get_info's (any pointer may be
- * NULL): n_modes, n_slots (|k|-sorted orbit records x 4 members, padding
- * included) and hist_bytes (the ring buffer of n_cut steps at `precision`).
+ * NULL): n_modes, n_slots (|k|-sorted records x 4 member slots, padding
+ * included; see sbim_get_info) and hist_bytes (the ring buffer of n_cut steps
+ * at `precision`).
  * Bins are grouped by exact |k| when L1 / L3 is a ratio of integers up to 4096.
  * SBIM_ERR_ARG for the grid, n_cut and precision rules of sbim_create.
  * Library utility: the paper has no counterpart.

@@ -107,6 +107,7 @@ struct sbim_ctx {
   int n_orb = 0, n_orb_pad = 0, lc = 1, nchunks = 1;
   int variant = 1;            // 0: register-prefetch loads, 1-3: TMA-staged history shapes
   int tile = sbim::kOrbitTile;  // orbits per CTA of the TMA convolution: 64, 128 or 256
+  bool halves = false;        // records may hold two |k| (half-record layout)
   int lags_per_cta = 0;       // 0: automatic
   size_t part_bytes = 0;
   double tab_h = 0;
@@ -138,7 +139,7 @@ struct sbim_ctx {
   int* d_lmax = nullptr;
   int* d_tile_lmax = nullptr;
   double window = 0.0;
-  std::vector<double> h_dT;   // |k| c_s dt per orbit (host copy)
+  std::vector<double> h_dT;   // |k| c_s dt per half record, [o][2] (host copy)
   void* d_io = nullptr;  // u, v, tau staging and zero spectra for sbim_step_host
   cudaStream_t io_stream = nullptr;          // sbim_step_host: copies in + forward FFT
   cudaEvent_t io_fork = nullptr, io_join = nullptr;
@@ -188,8 +189,20 @@ long long history_record_bytes(int prec) {
   }
 }
 
-// Group the half-spectrum bins into |k|-sorted orbits of <= 4 members.
-void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_orb) {
+// Group the half-spectrum bins into |k|-sorted records of 4 member slots made
+// of two halves of 2 slots; each half carries one |k| (q_half[2 r + h]).  The
+// members of one bin stay in one record.
+//   whole records (halves = false): a class of equal |k| fills records of its
+//     own (both halves carry its |k|) -- the layout of square grids, whose
+//     generic class {(a, b), (a, -b), (b, a), (b, -a)} is exactly one record;
+//   half records (halves = true): a class fills halves (a Nyquist bin's two
+//     virtual members take a half, the corner's four a whole record, other bins
+//     two to a half); its halves pair up into records of one |k|, and an odd one
+//     left over shares a record with the next class's leftover -- for
+//     rectangular planes, where most classes are pairs {(j1, j3), (j1, -j3)}
+//     and whole records would be half empty.
+void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half,
+                 bool halves) {
   long long ra, rb;
   period_ratio(c, ra, rb);
   const bool exact = ra > 0;
@@ -227,20 +240,38 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
     return exact ? x.ikey == y.ikey : x.dkey == y.dkey;
   };
 
+  const Member pad{-1, 1.0, 0.0, 0.0f};
+  struct Half {
+    Member m[2];
+    double q;
+  };
+  auto emit = [&](const Half& x, const Half& y) {
+    mem.push_back(x.m[0]);
+    mem.push_back(x.m[1]);
+    mem.push_back(y.m[0]);
+    mem.push_back(y.m[1]);
+    q_half.push_back(x.q);
+    q_half.push_back(y.q);
+  };
   std::vector<Member> cur;
-  auto flush = [&](double q) {
+  auto flush_whole = [&](double q) {
     if (cur.empty()) return;
-    while (cur.size() < 4) cur.push_back(Member{-1, 1.0, 0.0, 0.0f});
+    while (cur.size() < 4) cur.push_back(pad);
     mem.insert(mem.end(), cur.begin(), cur.end());
-    q_orb.push_back(q);
+    q_half.push_back(q);
+    q_half.push_back(q);
     cur.clear();
   };
+  bool have_left = false;
+  Half left{{pad, pad}, 0.0};
   size_t i = 0;
   while (i < recs.size()) {
     size_t j = i;
     while (j < recs.size() && same(recs[i], recs[j])) ++j;
     const double k1c = 2.0 * kPi * recs[i].j1 / c.L1, k3c = 2.0 * kPi * recs[i].j3 / c.L3;
     const double q = std::hypot(k1c, k3c);
+    std::vector<Half> hs;
+    std::vector<Member> singles;
     for (size_t t = i; t < j; ++t) {
       const Rec& r = recs[t];
       const bool ny1 = (r.j1 == c.n1 / 2), ny3 = (r.r3 == c.n3 / 2);
@@ -265,12 +296,48 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
           }
           grp.push_back(m);
         }
-      if (cur.size() + grp.size() > 4) flush(q);
-      cur.insert(cur.end(), grp.begin(), grp.end());
+      if (!halves) {   // whole records: fill this class's records of 4
+        if (cur.size() + grp.size() > 4) flush_whole(q);
+        cur.insert(cur.end(), grp.begin(), grp.end());
+      } else if (grp.size() == 1) {
+        singles.push_back(grp[0]);
+      } else {
+        for (size_t k = 0; k < grp.size(); k += 2) hs.push_back(Half{{grp[k], grp[k + 1]}, q});
+      }
     }
-    flush(q);
+    if (!halves) {
+      flush_whole(q);
+      i = j;
+      continue;
+    }
+    for (size_t k = 0; k < singles.size(); k += 2)
+      hs.push_back(Half{{singles[k], k + 1 < singles.size() ? singles[k + 1] : pad}, q});
+    size_t h = 0;
+    for (; h + 1 < hs.size(); h += 2) emit(hs[h], hs[h + 1]);
+    if (h < hs.size()) {
+      if (have_left) {
+        emit(left, hs[h]);
+        have_left = false;
+      } else {
+        left = hs[h];
+        have_left = true;
+      }
+    }
     i = j;
   }
+  if (have_left) emit(left, Half{{pad, pad}, 0.0});
+}
+
+// The record layout of a grid: whole records unless they would pad the
+// history by more than 3 % over the bins (rectangular planes), where half
+// records take their place.  Returns whether the layout has half records.
+bool plan_layout(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half) {
+  plan_orbits(c, mem, q_half, false);
+  if ((double)mem.size() <= 1.03 * c.nbins) return false;
+  mem.clear();
+  q_half.clear();
+  plan_orbits(c, mem, q_half, true);
+  return true;
 }
 
 // Lag chunking of the convolution grid: (n_orb_pad / 128) x nchunks CTAs,
@@ -353,21 +420,22 @@ int create_impl(sbim_ctx* c) {
   c->real_size = dbl ? 8 : 4;
 
   std::vector<Member> mem;
-  std::vector<double> q_orb;
-  plan_orbits(*c, mem, q_orb);
-  c->n_orb = (int)q_orb.size();
+  std::vector<double> q_half;
+  c->halves = plan_layout(*c, mem, q_half);
+  c->n_orb = (int)(q_half.size() / 2);
   c->n_orb_pad = (c->n_orb + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
   mem.resize((size_t)c->n_orb_pad * 4, Member{-1, 1.0, 0.0, 0.0f});
-  q_orb.resize(c->n_orb_pad, 0.0);
+  q_half.resize((size_t)c->n_orb_pad * 2, 0.0);
 
   // kernel-table resolution: cubic interpolation error ~ 0.0234 h^4 max|H''''|
   c->tab_h = dbl ? 1.0 / 512.0 : 1.0 / 64.0;
   double dT_max = 0.0;
-  std::vector<double> dT(c->n_orb_pad), muq(c->n_orb_pad);
-  std::vector<unsigned long long> ustep(c->n_orb_pad);
-  for (int o = 0; o < c->n_orb_pad; ++o) {
-    dT[o] = q_orb[o] * c->cs * c->dt;
-    muq[o] = c->mu * q_orb[o];
+  const int n_half = 2 * c->n_orb_pad;   // per half record: [o][2]
+  std::vector<double> dT(n_half), muq(n_half);
+  std::vector<unsigned long long> ustep(n_half);
+  for (int o = 0; o < n_half; ++o) {
+    dT[o] = q_half[o] * c->cs * c->dt;
+    muq[o] = c->mu * q_half[o];
     dT_max = std::max(dT_max, dT[o]);
     ustep[o] = (unsigned long long)std::llround(dT[o] / c->tab_h * 4294967296.0);
   }
@@ -390,7 +458,8 @@ int create_impl(sbim_ctx* c) {
   }
 
   if (choose_chunks(*c) != SBIM_OK) return SBIM_ERR_CUDA;
-  if (c->variant >= 1) CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant, c->tile));
+  if (c->variant >= 1)
+    CU(sbim::prepare_conv_tma(c->prec, c->kahan, c->variant, c->tile, c->halves));
 
   // history size
   c->plane_records = (long long)c->n_cut * 3 * c->n_orb_pad;
@@ -414,9 +483,9 @@ int create_impl(sbim_ctx* c) {
   CU(cudaMalloc(&c->d_bin, h_bin.size() * sizeof(int)));
   CU(cudaMalloc(&c->d_dir, h_dir.size() * (dbl ? sizeof(double2) : sizeof(float2))));
   CU(cudaMalloc(&c->d_wout, h_w.size() * sizeof(float)));
-  CU(cudaMalloc(&c->d_dT, c->n_orb_pad * c->real_size));
-  CU(cudaMalloc(&c->d_muq, c->n_orb_pad * c->real_size));
-  CU(cudaMalloc(&c->d_ustep, c->n_orb_pad * sizeof(unsigned long long)));
+  CU(cudaMalloc(&c->d_dT, 2 * c->n_orb_pad * c->real_size));
+  CU(cudaMalloc(&c->d_muq, 2 * c->n_orb_pad * c->real_size));
+  CU(cudaMalloc(&c->d_ustep, 2 * c->n_orb_pad * sizeof(unsigned long long)));
   CU(cudaMalloc(&c->d_tab64, (size_t)c->tab_n * 4 * sizeof(double)));
   if (!dbl) CU(cudaMalloc(&c->d_tab32, (size_t)c->tab_n * 4 * sizeof(float)));
   CU(cudaMalloc(&c->d_gl, 32 * sizeof(double)));
@@ -492,6 +561,7 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
   a.uhat = c->d_uhat;
   a.fhat = c->d_fhat;
   a.n_orb_pad = c->n_orb_pad;
+  a.halves = c->halves ? 1 : 0;
   a.nbins = c->nbins;
   a.n_cut = c->n_cut;
   a.lc = c->lc;
@@ -574,10 +644,10 @@ int sbim_plan(int n1, int n3, double L1, double L3, int n_cut, int precision,
   c.nh = n1 / 2 + 1;
   c.nbins = n3 * c.nh;
   std::vector<Member> mem;
-  std::vector<double> q_orb;
-  plan_orbits(c, mem, q_orb);
+  std::vector<double> q_half;
+  plan_layout(c, mem, q_half);
   const long long pad =
-      ((long long)q_orb.size() + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
+      ((long long)q_half.size() / 2 + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
   if (n_modes) *n_modes = c.nbins;
   if (n_slots) *n_slots = pad * 4;
   if (hist_bytes) *hist_bytes = (long long)n_cut * 3 * pad * history_record_bytes(precision);
@@ -672,7 +742,7 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
   if (repeat)
     CU(sbim::launch_repeat_lag0(a, c->prec, st));
   else if (c->variant >= 1)
-    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile));
+    CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile, c->halves));
   else
     CU(sbim::launch_conv(a, c->prec, c->kahan, st));
   if (e) CU(cudaEventRecord(e[2], st));
@@ -770,7 +840,7 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
     sbim::StepArgs a = step_args(c);
     a.uhat = zero_hat;
     if (c->variant >= 1)
-      CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile));
+      CU(sbim::launch_conv_tma(a, c->prec, c->kahan, c->variant, st, nullptr, c->tile, c->halves));
     else
       CU(sbim::launch_conv(a, c->prec, c->kahan, st));
     CU(cudaStreamWaitEvent(st, c->io_join, 0));
@@ -797,14 +867,15 @@ int sbim_set_window(sbim_handle h, double window) {
     h->window = 0;
     return SBIM_OK;
   }
-  std::vector<int> lm(h->n_orb_pad), tl(h->n_orb_pad / sbim::kOrbitTile, 1);
-  for (int o = 0; o < h->n_orb_pad; ++o) {
-    const double d = h->h_dT[o];
-    if (o >= h->n_orb) lm[o] = 1;                       // padding orbits
-    else if (d <= 0) lm[o] = h->n_cut;                  // k = 0
-    else lm[o] = (int)std::min<double>(h->n_cut, std::floor(window / d) + 1);
-    int& t = tl[o / sbim::kOrbitTile];
-    t = std::max(t, lm[o]);
+  // lags kept per half record; a tile's bound is the maximum over its halves
+  std::vector<int> lm(2 * h->n_orb_pad), tl(h->n_orb_pad / sbim::kOrbitTile, 1);
+  for (int x = 0; x < 2 * h->n_orb_pad; ++x) {
+    const double d = h->h_dT[x];
+    if (x >= 2 * h->n_orb) lm[x] = 1;                   // padding records
+    else if (d <= 0) lm[x] = h->n_cut;                  // k = 0 (and padding halves)
+    else lm[x] = (int)std::min<double>(h->n_cut, std::floor(window / d) + 1);
+    int& t = tl[(x / 2) / sbim::kOrbitTile];
+    t = std::max(t, lm[x]);
   }
   if (!h->d_lmax) CU(cudaMalloc(&h->d_lmax, lm.size() * sizeof(int)));
   if (!h->d_tile_lmax) CU(cudaMalloc(&h->d_tile_lmax, tl.size() * sizeof(int)));
@@ -858,7 +929,7 @@ int sbim_set_conv_config(sbim_handle h, int variant, int lags_per_cta) {
   h->variant = variant;
   h->lags_per_cta = lags_per_cta;
   if (variant >= 1) {
-    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, variant, h->tile);
+    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, variant, h->tile, h->halves);
     if (e != cudaSuccess) {
       h->variant = old_v;
       h->lags_per_cta = old_l;
@@ -885,7 +956,7 @@ int sbim_set_conv_tile(sbim_handle h, int orbits_per_cta) {
   const int old_t = h->tile, old_lc = h->lc, old_nc = h->nchunks;
   h->tile = orbits_per_cta;
   if (h->variant >= 1) {
-    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, h->variant, h->tile);
+    const cudaError_t e = sbim::prepare_conv_tma(h->prec, h->kahan, h->variant, h->tile, h->halves);
     if (e != cudaSuccess) {
       h->tile = old_t;
       return fail(SBIM_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));

@@ -17,6 +17,7 @@ struct sbim_batch_ctx {
   int nb = 0, prec = SBIM_FP32, kahan = 1, shape = 2;
   int tile = sbim::kOrbitTile;   // orbits per CTA of the batched convolution
   int lags = 0;                  // lags per work item last configured
+  bool halves = false;           // some member's records hold two |k|
   bool per_item = false;    // one CTA per work item instead of persistent CTAs
   bool owns = true;
   cudaStream_t stream = nullptr;
@@ -112,7 +113,9 @@ int configure(sbim_batch_ctx* b, int shape, int lags) {
     const int rc = sbim_set_conv_config(b->h[i], shape, lags);
     if (rc != SBIM_OK) return rc;
   }
-  BCU(sbim::prepare_conv_tma(b->prec, b->kahan, shape, b->tile));
+  b->halves = false;
+  for (int i = 0; i < b->nb; ++i) b->halves = b->halves || sbim::handle_step_args(b->h[i]).halves;
+  BCU(sbim::prepare_conv_tma(b->prec, b->kahan, shape, b->tile, b->halves));
   b->shape = shape;
   b->lags = lags;
   std::vector<sbim::StepArgs> args(b->nb);
@@ -189,7 +192,7 @@ int enqueue(sbim_batch_ctx* b, const void* const* u, const void* const* v, void*
   bl.ctas = b->ctas;
   bl.items = b->per_item ? b->total_items : 0;
   const sbim::StepArgs a0 = sbim::handle_step_args(b->h[0]);
-  BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl, b->tile));
+  BCU(sbim::launch_conv_tma(a0, b->prec, b->kahan, b->shape, b->stream, &bl, b->tile, b->halves));
   BCU(sbim::launch_assemble_batch(bl, b->total_tiles, b->prec, b->kahan, b->stream));
   rc = fork(b);
   for (int i = 0; i < b->nb && rc == SBIM_OK; ++i) {

@@ -1,6 +1,7 @@
 // Per-step kernels of the spectral boundary integral update (Section 2.3, Eq. (SBI)).
 //
-//  conv_kernel     For every orbit (four Fourier-bin members sharing |k|) and one
+//  conv_kernel     For every record (four Fourier-bin member slots in two halves,
+//                  the members of a half sharing |k|) and one
 //                  chunk of lags: rotate the current spectra into the
 //                  (xi, 2, perp) frame of each member and write them into the
 //                  history ring slot (chunk 0 only), then accumulate the five
@@ -10,8 +11,8 @@
 //                     C12b = sum_m w12(m) D_xi[n-m]
 //                  with trapezoid weights w(m) = dT H(m dT) (half at m = 0),
 //                  dT = |k| c_s dt.  The weights are interpolated from a table of
-//                  H(T) (cubic Lagrange), once per orbit and lag for all four
-//                  members, so they cost no HBM bytes.
+//                  H(T) (cubic Lagrange), once per half and lag (once per record
+//                  when its halves share |k|), so they cost no HBM bytes.
 //  assemble_kernel Sum the chunk partials in chunk order, add the instantaneous
 //                  in-plane coupling (2 - eta), apply -side mu |k| to the diagonal
 //                  terms, rotate back to (1, 2, 3) and write the output spectrum
@@ -32,8 +33,10 @@ using namespace dev;
 template <class S> struct MinBlocks { static constexpr int value = 3; };
 template <> struct MinBlocks<StoreF64> { static constexpr int value = 1; };
 
-template <class S, int KAHAN>
-__global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(const StepArgs a) {
+// (The half-record variants, with a second weight set, are sized for 2 CTAs/SM.)
+template <class S, int KAHAN, bool HALVES>
+__global__ void __launch_bounds__(kOrbitTile, HALVES && MinBlocks<S>::value > 2 ? 2 : MinBlocks<S>::value)
+conv_kernel(const StepArgs a) {
   using R = typename S::real;
   using C = typename S::cplx;
   using T4 = typename S::tab4;
@@ -45,10 +48,12 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
   const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[blockIdx.x]) : n_valid;
   if (m0 >= m_end) return;
   const int m1 = min(m0 + a.lc, m_end);
-  const int lo = a.lmax ? a.lmax[o] : 0x7fffffff;   // this orbit's truncation
+  // the two halves' truncation, lag spacing in T and table step
+  const int lo0 = a.lmax ? a.lmax[2 * o] : 0x7fffffff, lo1 = a.lmax ? a.lmax[2 * o + 1] : 0x7fffffff;
   const int sn = (int)(n % a.n_cut);
-  const R dT = reinterpret_cast<const R*>(a.dT)[o];
-  const unsigned long long us = a.ustep[o];
+  const R dT0 = reinterpret_cast<const R*>(a.dT)[2 * o], dT1 = reinterpret_cast<const R*>(a.dT)[2 * o + 1];
+  const unsigned long long us0 = a.ustep[2 * o], us1 = a.ustep[2 * o + 1];
+  const bool same = !HALVES || us0 == us1;   // whole-record plans: always one |k|
   const T4* tab = reinterpret_cast<const T4*>(a.table);
   const long long orb = a.n_orb_pad;
   const long long plane = a.slot_stride;
@@ -68,15 +73,21 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
       S::store(a.hist, ((long long)sn * 3 + c) * orb + o, plane, D[c]);
       S::round(D[c]);
     }
-    R w[4];
-    lag_weights(tab, 0ull, dT * (R)0.5, w);
-    accumulate<KAHAN>(acc, cmp, w, D);
+    R w0[4], w1[4];
+    lag_weights(tab, 0ull, dT0 * (R)0.5, w0);
+    if (same) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w1[q] = w0[q];
+    } else {
+      lag_weights(tab, 0ull, dT1 * (R)0.5, w1);
+    }
+    accumulate<KAHAN>(acc, cmp, w0, w1, D);
     m = 1;
   }
   if (m < m1) {
     int slot = sn - m;
     if (slot < 0) slot += a.n_cut;
-    unsigned long long u = (unsigned long long)m * us;
+    unsigned long long u0 = (unsigned long long)m * us0, u1 = (unsigned long long)m * us1;
     C Dn[3][4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) S::load(a.hist, ((long long)slot * 3 + c) * orb + o, plane, Dn[c]);
@@ -91,10 +102,17 @@ __global__ void __launch_bounds__(kOrbitTile, MinBlocks<S>::value) conv_kernel(c
 #pragma unroll
         for (int c = 0; c < 3; ++c) S::load(a.hist, ((long long)slot * 3 + c) * orb + o, plane, Dn[c]);
       }
-      R w[4];
-      lag_weights(tab, u, m < lo ? dT : (R)0, w);
-      u += us;
-      accumulate<KAHAN>(acc, cmp, w, D);
+      R w0[4], w1[4];
+      lag_weights(tab, u0, m < lo0 ? dT0 : (R)0, w0);
+      if (same) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w1[q] = w0[q];
+      } else {
+        lag_weights(tab, u1, m < lo1 ? dT1 : (R)0, w1);
+      }
+      u0 += us0;
+      u1 += us1;
+      accumulate<KAHAN>(acc, cmp, w0, w1, D);
     }
   }
   R* part = reinterpret_cast<R*>(a.part);
@@ -115,7 +133,8 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   const int m_end = a.tile_lmax ? min(n_valid, a.tile_lmax[o / kOrbitTile]) : n_valid;
   const int nch = (m_end + a.lc - 1) / a.lc;
   const long long orb = a.n_orb_pad;
-  const R muq = reinterpret_cast<const R*>(a.muq)[o];
+  const R muq0 = reinterpret_cast<const R*>(a.muq)[2 * o];
+  const R muq1 = reinterpret_cast<const R*>(a.muq)[2 * o + 1];
   const R sd = (R)a.side;
   const R inst = (R)(2.0 - a.eta);
   const R* part = reinterpret_cast<const R*>(a.part);
@@ -160,6 +179,7 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   for (int g = 0; g < 4; ++g) {
     const int b = a.bin[o * 4 + g];
     if (b < 0) continue;
+    const R muq = g < 2 ? muq0 : muq1;
     const R* v = sum[g];
     const C dxi = D[0][g], d2 = D[1][g];
     // F_xi = -side mu q C11 + i mu q [(2 - eta) D_2 + C12a]
@@ -251,9 +271,9 @@ __global__ void __launch_bounds__(256) weights64_kernel(const StepArgs a, Double
   if (i >= total) return;
   const int o = (int)(i % a.n_orb_pad);
   const long long m = i / a.n_orb_pad;
-  double w[4];
-  lag_weights(reinterpret_cast<const Double4*>(a.table), (unsigned long long)m * a.ustep[o],
-              reinterpret_cast<const double*>(a.dT)[o], w);
+  double w[4];   // half 0 of the record (the kernel interpolates a differing half 1)
+  lag_weights(reinterpret_cast<const Double4*>(a.table), (unsigned long long)m * a.ustep[2 * o],
+              reinterpret_cast<const double*>(a.dT)[2 * o], w);
   Double4 r;
   r.x = w[0]; r.y = w[1]; r.z = w[2]; r.w = w[3];
   out[i] = r;
@@ -298,12 +318,15 @@ __global__ void __launch_bounds__(kOrbitTile) repeat_lag0_kernel(const StepArgs 
     S::store(a.hist, rec, a.slot_stride, Dn[c]);
     S::round(Dn[c]);
   }
-  R w[4];
+  R w0[4], w1[4];
   lag_weights(reinterpret_cast<const T4*>(a.table), 0ull,
-              reinterpret_cast<const R*>(a.dT)[o] * (R)0.5, w);
+              reinterpret_cast<const R*>(a.dT)[2 * o] * (R)0.5, w0);
+  lag_weights(reinterpret_cast<const T4*>(a.table), 0ull,
+              reinterpret_cast<const R*>(a.dT)[2 * o + 1] * (R)0.5, w1);
   R* part = reinterpret_cast<R*>(a.part);
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
+    const R* w = g < 2 ? w0 : w1;
     C x, d2, dp;
     x.x = Dn[0][g].x - Do[0][g].x;  x.y = Dn[0][g].y - Do[0][g].y;
     d2.x = Dn[1][g].x - Do[1][g].x; d2.y = Dn[1][g].y - Do[1][g].y;
@@ -324,7 +347,10 @@ __global__ void rewind_kernel(long long* step) {
 template <class S, int KAHAN>
 cudaError_t conv_dispatch(const StepArgs& a, cudaStream_t st) {
   const dim3 grid(a.n_orb_pad / kOrbitTile, a.nchunks);
-  conv_kernel<S, KAHAN><<<grid, kOrbitTile, 0, st>>>(a);
+  if (a.halves)
+    conv_kernel<S, KAHAN, true><<<grid, kOrbitTile, 0, st>>>(a);
+  else
+    conv_kernel<S, KAHAN, false><<<grid, kOrbitTile, 0, st>>>(a);
   return cudaGetLastError();
 }
 

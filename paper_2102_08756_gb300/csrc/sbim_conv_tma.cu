@@ -30,33 +30,35 @@ cudaError_t launch_wait_selftest(int* err, cudaStream_t st) {
 }
 
 cudaError_t launch_conv_tma_f32(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile);
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves);
 cudaError_t launch_conv_tma_bf16x2(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile);
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves);
 cudaError_t launch_conv_tma_bf16(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile);
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves);
 cudaError_t launch_conv_tma_f64(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile);
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves);
 
 static cudaError_t dispatch(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t st, const BatchLaunch* batch, bool prep, int tile) {
+                            cudaStream_t st, const BatchLaunch* batch, bool prep, int tile,
+                            bool halves) {
   switch (precision) {
-    case SBIM_FP64: return launch_conv_tma_f64(a, 0, shape, st, batch, prep, tile);
-    case SBIM_FP32: return launch_conv_tma_f32(a, kahan, shape, st, batch, prep, tile);
-    case SBIM_BF16X2: return launch_conv_tma_bf16x2(a, kahan, shape, st, batch, prep, tile);
-    case SBIM_BF16: return launch_conv_tma_bf16(a, kahan, shape, st, batch, prep, tile);
+    case SBIM_FP64: return launch_conv_tma_f64(a, 0, shape, st, batch, prep, tile, halves);
+    case SBIM_FP32: return launch_conv_tma_f32(a, kahan, shape, st, batch, prep, tile, halves);
+    case SBIM_BF16X2:
+      return launch_conv_tma_bf16x2(a, kahan, shape, st, batch, prep, tile, halves);
+    case SBIM_BF16: return launch_conv_tma_bf16(a, kahan, shape, st, batch, prep, tile, halves);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
-                            cudaStream_t st, const BatchLaunch* batch, int tile) {
-  return dispatch(a, precision, kahan, shape, st, batch, false, tile);
+                            cudaStream_t st, const BatchLaunch* batch, int tile, bool halves) {
+  return dispatch(a, precision, kahan, shape, st, batch, false, tile, halves);
 }
 
-cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile) {
+cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile, bool halves) {
   const StepArgs none{};
-  return dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile);
+  return dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile, halves);
 }
 
 int conv_tma_ctas_per_sm(int precision, int shape, int tile) {

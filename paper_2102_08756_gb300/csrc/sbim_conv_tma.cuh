@@ -93,8 +93,12 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 // (hides their L2 latency, at KS x 16 floats of registers per thread).  The
 // compensated BF16 kernels, whose unpacked records and Kahan terms already
 // fill the register file, interpolate each stage's weights in place instead.
-template <class S, int KAHAN> struct PrefetchNodes { static constexpr bool value = true; };
-template <bool LO> struct PrefetchNodes<dev::StoreBF16<LO>, 1> {
+// Half-record kernels (whose second weight set takes the registers) interpolate
+// in place too.
+template <class S, int KAHAN, bool HALVES> struct PrefetchNodes {
+  static constexpr bool value = !HALVES;
+};
+template <bool LO, bool HALVES> struct PrefetchNodes<dev::StoreBF16<LO>, 1, HALVES> {
   static constexpr bool value = false;
 };
 
@@ -152,7 +156,7 @@ __device__ __forceinline__ void interp_nodes(const T4 nd[4], unsigned long long 
 // over from item to item through the running stage count `gstage` (stage s of
 // this item is global stage gstage + s: buffer (gstage + s) % NS, parity
 // ((gstage + s) / NS) & 1).  Returns false if a bounded wait gave up.
-template <class S, int KAHAN, int NS, int KS, int TILE>
+template <class S, int KAHAN, int NS, int KS, int TILE, bool HALVES>
 __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int chunk,
                                               unsigned char* smem, unsigned long long* full,
                                               unsigned& gstage) {
@@ -182,10 +186,15 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
   }
   if (m0 >= m_end) return true;   // uniform over the CTA
   const int m1 = min(m0 + a.lc, m_end);
-  const int lo = a.lmax ? a.lmax[o] : 0x7fffffff;   // this orbit's truncation
+  // the record's two halves: truncation, lag spacing in T and table step of each
+  // (equal when the record holds one |k|, the usual case on square grids)
+  const int lo = a.lmax ? a.lmax[2 * o] : 0x7fffffff;
+  const int lo1 = a.lmax ? a.lmax[2 * o + 1] : 0x7fffffff;
   const int sn = (int)(n % a.n_cut);
-  const R dT = reinterpret_cast<const R*>(a.dT)[o];
-  const unsigned long long us = a.ustep[o];
+  const R dT = reinterpret_cast<const R*>(a.dT)[2 * o];
+  const R dT1 = reinterpret_cast<const R*>(a.dT)[2 * o + 1];
+  const unsigned long long us = a.ustep[2 * o], us1 = a.ustep[2 * o + 1];
+  const bool same = !HALVES || us == us1;   // whole-record plans: always one |k|
   const T4* tab = reinterpret_cast<const T4*>(a.table);
   const long long orb = a.n_orb_pad;
 
@@ -209,8 +218,14 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       S::store(a.hist, ((long long)sn * 3 + c) * orb + o, a.slot_stride, D[c]);
       S::round(D[c]);
     }
-    R w[4];
-    lag_weights(tab, 0ull, dT * (R)0.5, w);
+    R w0[4], w1[4];
+    lag_weights(tab, 0ull, dT * (R)0.5, w0);
+    if (same) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w1[q] = w0[q];
+    } else {
+      lag_weights(tab, 0ull, dT1 * (R)0.5, w1);
+    }
     C Dp[3][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -220,7 +235,25 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
 #pragma unroll
           for (int c = 0; c < 3; ++c) Dp[c][j] = D[c][((j / MPC + r) % NCH) * MPC + j % MPC];
         }
-    accumulate<KAHAN>(acc, cmp, w, Dp);
+    // slot j holds member ((j / MPC + rot) % NCH) MPC + j % MPC, of half member / 2
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool h1 = ((j / MPC + rot) % NCH) * MPC + j % MPC >= 2;
+      R wj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wj[q] = h1 ? w1[q] : w0[q];
+      const C dxi = Dp[0][j], d2 = Dp[1][j], dp = Dp[2][j];
+      kadd<KAHAN>(acc[j][0], cmp[j][0], wj[0], dxi.x);
+      kadd<KAHAN>(acc[j][1], cmp[j][1], wj[0], dxi.y);
+      kadd<KAHAN>(acc[j][2], cmp[j][2], wj[2], dp.x);
+      kadd<KAHAN>(acc[j][3], cmp[j][3], wj[2], dp.y);
+      kadd<KAHAN>(acc[j][4], cmp[j][4], wj[1], d2.x);
+      kadd<KAHAN>(acc[j][5], cmp[j][5], wj[1], d2.y);
+      kadd<KAHAN>(acc[j][6], cmp[j][6], wj[3], d2.x);
+      kadd<KAHAN>(acc[j][7], cmp[j][7], wj[3], d2.y);
+      kadd<KAHAN>(acc[j][8], cmp[j][8], wj[3], dxi.x);
+      kadd<KAHAN>(acc[j][9], cmp[j][9], wj[3], dxi.y);
+    }
     mf = 1;
   }
 
@@ -256,7 +289,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
     if (tid == 0)
       for (int s = 0; s < min(NS - 1, nst); ++s) issue(s);
 
-    constexpr bool PF = PrefetchNodes<S, KAHAN>::value;
+    constexpr bool PF = PrefetchNodes<S, KAHAN, HALVES>::value;
     // weights of stage 0 (prefetching shapes)
     R wn[KS][4];
     if constexpr (PF) if (!pre) {
@@ -333,10 +366,35 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
         }
       }
 
+      // half 1's weights: half 0's when the record holds one |k|, else
+      // interpolated here (half 0's are prefetched, precomputed or in place)
+      R w1[KS][4];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (same) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w1[k][q] = w[k][q];
+        } else if (mb + k < m1 && mb + k < lo1) {
+          lag_weights(tab, (unsigned long long)(mb + k) * us1, dT1, w1[k]);
+        } else {
+          w1[k][0] = w1[k][1] = w1[k][2] = w1[k][3] = (R)0;
+        }
+      }
+
       const unsigned char* stage = smem + (gi % NS) * STAGE;
 #pragma unroll
       for (int r = 0; r < NCH; ++r) {
         const int ch = (r + rot) % NCH;
+        // a chunk of <= 2 members lies in one half (ch MPC / 2); a 4-member
+        // chunk spans both, selected per member below
+        R wc[KS][4];
+        if constexpr (MPC <= 2) {
+          const bool h1 = ch * MPC >= 2;
+#pragma unroll
+          for (int k = 0; k < KS; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) wc[k][q] = h1 ? w1[k][q] : w[k][q];
+        }
         C D[KS][3][MPC];
 #pragma unroll
         for (int k = 0; k < KS; ++k)
@@ -366,7 +424,9 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
                                : make_float2(acc[g][f], acc[g][f + 1]);
 #pragma unroll
               for (int k = 0; k < KS; ++k) {
-                const R wk = w[k][kern[f]];
+                R wk;
+                if constexpr (MPC <= 2) wk = wc[k][kern[f]];
+                else wk = j < 2 ? w[k][kern[f]] : w1[k][kern[f]];
                 y = fma2(make_float2(wk, wk), D[k][comp[f]][j], y);
               }
               if (KAHAN) {
@@ -389,7 +449,10 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
 #pragma unroll
               for (int k = 0; k < KS; ++k) {
                 const C d = D[k][comp[f]][j];
-                y = fma(w[k][kern[f]], (f & 1) ? d.y : d.x, y);
+                R wk;
+                if constexpr (MPC <= 2) wk = wc[k][kern[f]];
+                else wk = j < 2 ? w[k][kern[f]] : w1[k][kern[f]];
+                y = fma(wk, (f & 1) ? d.y : d.x, y);
               }
               if (KAHAN) {
                 const R t = acc[g][f] + y;
@@ -449,13 +512,13 @@ __device__ __forceinline__ void init_barriers(unsigned long long* full) {
 }
 
 // One CTA per (orbit tile, lag chunk) of one update.
-template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 __global__ void __launch_bounds__(TILE, MINB) conv_tma_kernel(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full[NS];
   init_barriers<NS>(full);
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS, TILE>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
 }
 
 // Persistent CTAs over the (update, tile, chunk) items of a batch of updates
@@ -463,7 +526,7 @@ __global__ void __launch_bounds__(TILE, MINB) conv_tma_kernel(const StepArgs a) 
 // order (item_prefix[s] .. item_prefix[s+1]-1 belong to update s, tile-major
 // within each lag chunk).  Every item writes its own partial sums, so the
 // result does not depend on which CTA ran it.
-template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 __global__ void __launch_bounds__(TILE, MINB)
 conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
                       int nb, int* counter) {
@@ -491,7 +554,8 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
     }
     __syncthreads();
     if (s_item >= total) break;
-    if (!conv_tma_item<S, KAHAN, NS, KS, TILE>(s_args, s_tile, s_chunk, smem, full, gstage)) return;
+    if (!conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage))
+      return;
   }
 }
 
@@ -499,7 +563,7 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
 // scheduler hands the items out; no work counter, and no barrier phases carried
 // from item to item, so its register needs are those of the single-update
 // kernel).  Same item order as the persistent kernel.
-template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 __global__ void __launch_bounds__(TILE, MINB)
 conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__ item_prefix,
                       int nb) {
@@ -519,24 +583,24 @@ conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__
   }
   init_barriers<NS>(full);   // its __syncthreads publishes the item too
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS, TILE>(s_args, s_tile, s_chunk, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage);
 }
 
 // Launch one instantiation (sets the dynamic shared-memory attribute once).
 // With `batch` set, launches over the batch's items instead: one CTA per item
 // when `batch->items` > 0, else the persistent kernel on `batch->ctas` CTAs.
-template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 cudaError_t prepare_shape() {
   static bool attr_set = false;
   constexpr int bytes = smem_bytes<S, NS, KS, TILE>();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE>,
+      e = cudaFuncSetAttribute(conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE>,
+      e = cudaFuncSetAttribute(conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -545,39 +609,47 @@ cudaError_t prepare_shape() {
 }
 
 // With `batch` null and `prepare_only` set, only sets the kernels' attributes.
-template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 cudaError_t launch_shape(const StepArgs& a, cudaStream_t st, const BatchLaunch* batch = nullptr,
                          bool prepare_only = false) {
   constexpr int bytes = smem_bytes<S, NS, KS, TILE>();
-  const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB, TILE>();
+  const cudaError_t pe = prepare_shape<S, KAHAN, NS, KS, MINB, TILE, HALVES>();
   if (pe != cudaSuccess || prepare_only) return pe;
   if (batch && batch->items > 0) {
-    conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE><<<batch->items, TILE, bytes, st>>>(
+    conv_tma_items_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES><<<batch->items, TILE, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb);
   } else if (batch) {
-    conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE><<<batch->ctas, TILE, bytes, st>>>(
+    conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES><<<batch->ctas, TILE, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb, batch->counter);
   } else {
     if (a.n_orb_pad % TILE != 0) return cudaErrorInvalidValue;
     const dim3 grid(a.n_orb_pad / TILE, a.nchunks);
-    conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE><<<grid, TILE, bytes, st>>>(a);
+    conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES><<<grid, TILE, bytes, st>>>(a);
   }
   return cudaGetLastError();
 }
 
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE>
+cudaError_t launch_halves(bool halves, const StepArgs& a, cudaStream_t st,
+                          const BatchLaunch* batch, bool prepare_only) {
+  return halves ? launch_shape<S, KAHAN, NS, KS, MINB, TILE, true>(a, st, batch, prepare_only)
+                : launch_shape<S, KAHAN, NS, KS, MINB, TILE, false>(a, st, batch, prepare_only);
+}
+
 // A pipeline shape (sized for 128-orbit tiles: MINB resident CTAs per SM) at the
-// orbit tile `tile`.
+// orbit tile `tile`, for records of one |k| or (halves) of two.
 template <class S, int KAHAN, int NS, int KS, int MINB>
-cudaError_t launch_tiles(int tile, const StepArgs& a, cudaStream_t st, const BatchLaunch* batch,
-                         bool prepare_only) {
+cudaError_t launch_tiles(int tile, bool halves, const StepArgs& a, cudaStream_t st,
+                         const BatchLaunch* batch, bool prepare_only) {
   switch (tile) {
     case 64:
-      return launch_shape<S, KAHAN, NS, KS, minb_for_tile(MINB, 64), 64>(a, st, batch, prepare_only);
+      return launch_halves<S, KAHAN, NS, KS, minb_for_tile(MINB, 64), 64>(halves, a, st, batch,
+                                                                         prepare_only);
     case 128:
-      return launch_shape<S, KAHAN, NS, KS, MINB, 128>(a, st, batch, prepare_only);
+      return launch_halves<S, KAHAN, NS, KS, MINB, 128>(halves, a, st, batch, prepare_only);
     case 256:
-      return launch_shape<S, KAHAN, NS, KS, minb_for_tile(MINB, 256), 256>(a, st, batch,
-                                                                          prepare_only);
+      return launch_halves<S, KAHAN, NS, KS, minb_for_tile(MINB, 256), 256>(halves, a, st, batch,
+                                                                           prepare_only);
     default:
       return cudaErrorInvalidValue;
   }

@@ -8,20 +8,20 @@ namespace sbim {
 
 template <int KAHAN>
 static cudaError_t shapes_bf16x2(const StepArgs& a, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile) {
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves) {
   using S = dev::StoreBF16<true>;
   switch (shape) {
-    case 1: return tma::launch_tiles<S, KAHAN, 4, 2, 2>(tile, a, st, batch, prep);
-    case 2: return tma::launch_tiles<S, KAHAN, 3, 2, 3>(tile, a, st, batch, prep);
-    case 3: return tma::launch_tiles<S, KAHAN, 2, 4, 2>(tile, a, st, batch, prep);
+    case 1: return tma::launch_tiles<S, KAHAN, 4, 2, 2>(tile, halves, a, st, batch, prep);
+    case 2: return tma::launch_tiles<S, KAHAN, 3, 2, 3>(tile, halves, a, st, batch, prep);
+    case 3: return tma::launch_tiles<S, KAHAN, 2, 4, 2>(tile, halves, a, st, batch, prep);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_conv_tma_bf16x2(const StepArgs& a, int kahan, int shape, cudaStream_t st,
-                                 const BatchLaunch* batch, bool prep, int tile) {
-  return kahan ? shapes_bf16x2<1>(a, shape, st, batch, prep, tile)
-               : shapes_bf16x2<0>(a, shape, st, batch, prep, tile);
+                                 const BatchLaunch* batch, bool prep, int tile, bool halves) {
+  return kahan ? shapes_bf16x2<1>(a, shape, st, batch, prep, tile, halves)
+               : shapes_bf16x2<0>(a, shape, st, batch, prep, tile, halves);
 }
 
 }  // namespace sbim

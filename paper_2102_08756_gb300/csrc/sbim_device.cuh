@@ -217,12 +217,14 @@ __device__ __forceinline__ void kadd(R& s, R& c, R w, R x) {
   }
 }
 
-// acc[g][*] += weights (11, 22, 33, 12) applied to member g's (xi, 2, perp) values
+// acc[g][*] += weights (11, 22, 33, 12) applied to member g's (xi, 2, perp)
+// values; members 0, 1 (half 0 of the record) take w0, members 2, 3 take w1.
 template <int KAHAN, class R, class C>
 __device__ __forceinline__ void accumulate(R (&acc)[4][kFields], R (&cmp)[4][kFields],
-                                           const R w[4], const C (&D)[3][4]) {
+                                           const R w0[4], const R w1[4], const C (&D)[3][4]) {
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
+    const R* w = g < 2 ? w0 : w1;
     const C dxi = D[0][g], d2 = D[1][g], dp = D[2][g];
     kadd<KAHAN>(acc[g][0], cmp[g][0], w[0], dxi.x);
     kadd<KAHAN>(acc[g][1], cmp[g][1], w[0], dxi.y);

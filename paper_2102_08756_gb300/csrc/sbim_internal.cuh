@@ -3,9 +3,14 @@
 // Spectral layout used by every kernel (Section 2.3, spectral evaluation of s_i):
 //   * Half spectra from the R2C transform: [3][n3][n1/2+1] complex, bin b =
 //     r3 * (n1/2+1) + j1.
-//   * "Orbits": the library groups the Fourier bins by |k| (all bins of one
-//     orbit share |k|, hence the kernel arguments T = m |k| c_s dt and the
-//     convolution weights), four "members" per orbit.  A member is one bin seen
+//   * "Orbits" (records): the library groups the Fourier bins by |k| into
+//     records of four "members" in two halves of two; the members of a half
+//     share |k|, hence the kernel arguments T = m |k| c_s dt and the convolution
+//     weights.  Per-record |k| data (dT, ustep, muq, lmax) is stored per half,
+//     [record][2].  Whole-record plans (StepArgs::halves = 0, square grids) give
+//     both halves one |k|; half-record plans pair halves of two classes where
+//     classes of two bins would otherwise leave half of a record empty
+//     (rectangular planes).  A member is one bin seen
 //     along one in-plane direction e = k/|k|; a bin on a Nyquist line appears as
 //     two (or, at the corner, four) members whose directions differ in the sign
 //     of the aliased component, each weighted 1/2 (1/4), which keeps only the
@@ -49,6 +54,7 @@ struct StepArgs {
   void* fhat;                      // [3][nbins] output spectra (scaled 1/(n1 n3))
   // sizes (host values)
   int n_orb_pad;
+  int halves;                      // 1: a record's two halves may hold different |k|
   int nbins;
   int n_cut;
   int lc;                          // lags per chunk
@@ -78,13 +84,15 @@ cudaError_t launch_assemble_batch(const BatchLaunch& b, int total_tiles, int pre
 // residency the launch is sized for.
 // shape 1..3 selects the pipeline (stages, lags per stage, CTAs per SM); tile the
 // orbits per CTA (64, 128 or 256; n_orb_pad must be a multiple of it).
+// halves: the records may hold two |k| (one per half; see StepArgs::halves).
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
                             cudaStream_t s, const BatchLaunch* batch = nullptr,
-                            int tile = kOrbitTile);
+                            int tile = kOrbitTile, bool halves = false);
 int conv_tma_ctas_per_sm(int precision, int shape, int tile = kOrbitTile);
 // Set the shared-memory attributes of a shape's kernels (done before any launch,
 // so that launches can be captured in a CUDA graph).
-cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile = kOrbitTile);
+cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile = kOrbitTile,
+                             bool halves = false);
 // One CTA whose bounded mbarrier wait can never complete (sbim_selftest_wait_timeout).
 cudaError_t launch_wait_selftest(int* err, cudaStream_t st);
 cudaError_t launch_assemble(const StepArgs& a, int precision, int kahan, cudaStream_t s);

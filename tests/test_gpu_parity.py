@@ -132,6 +132,23 @@ def test_orbit_tiles_match_oracle(precision, kahan, tile, variant):
         assert et < TOL[precision], (n1, n3, et)
 
 
+@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("bf16x2", 1), ("fp32", 0)])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_whole_record_layout_matches_oracle(precision, kahan, variant):
+    """384 x 384: the smallest square grid whose whole-record layout (every
+    record one class of equal |k|) pads under 3 %, so it runs the whole-record
+    kernels that the benchmark grids use; every mode, ring wrap-around, both
+    half-spaces, against the oracle."""
+    from tests._layout import grid_records
+    n, dx = 384, 100.0
+    records, halves = grid_records(n, n, n * dx, n * dx)
+    assert not halves
+    for side, n_cut in ((1, 4), (-1, 7)):
+        es, et = run_parity(n, n, n * dx, n * dx, n_cut, side, n_cut + 3, precision, kahan,
+                            seed=n + n_cut + variant, spectrum="k2", variant=variant)
+        assert es < TOL[precision] and et < TOL[precision], (side, es, et)
+
+
 def test_orbit_tile_must_divide_the_records():
     from paper_2102_08756_gb300.sbim import SBIM, SBIMError
     g = SBIM(48, 32, 4800.0, 3200.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)   # 384 records

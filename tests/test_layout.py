@@ -6,7 +6,7 @@ of each precision; invalid grids are rejected."""
 import pytest
 
 from paper_2102_08756_gb300 import _build
-from tests._layout import expected_slots
+from tests._layout import _classes, expected_slots, grid_records
 
 REC_BYTES = {"fp64": 64, "fp32": 32, "bf16x2": 32, "bf16": 16}
 
@@ -34,9 +34,12 @@ def test_slots_match_exact_wavenumber_classes(plan, n1, n3, L1, L3):
 
 
 def test_tpv3_plane_and_square_headline_grid(plan):
-    # the 1024 x 512 plane of the TPV3 runs (dx = 50 m): 1.20x the bins
+    # the 1024 x 512 plane of the TPV3 runs (dx = 50 m): whole records would take
+    # 314,568 slots (1.20x the bins, most classes being pairs); half records
+    # take 264,704 with the tile padding (1.008x)
     p = plan(1024, 512, 51200.0, 25600.0, 1600, "fp32")
-    assert p["n_modes"] == 262656 and p["n_slots"] == 314880
+    assert p["n_modes"] == 262656 and p["n_slots"] == 264704
+    assert p["n_slots"] <= 1.03 * p["n_modes"]
     # the 1024^2 boundary with a 4096-lag FP32 history: 52.04 GB
     q = plan(1024, 1024, 102400.0, 102400.0, 4096, "fp32")
     assert q["n_slots"] == 529408 and q["hist_bytes"] == 52042924032
@@ -60,3 +63,26 @@ def test_plan_rejects_bad_arguments(plan, args):
     from paper_2102_08756_gb300.sbim import SBIMError
     with pytest.raises(SBIMError):
         plan(*args)
+
+
+@pytest.mark.parametrize("n1,n3,L1,L3", [(16, 12, 1600.0, 1200.0), (64, 32, 6400.0, 3200.0),
+                                        (32, 32, 3200.0, 3200.0), (384, 384, 38400.0, 38400.0),
+                                        (6, 2, 600.0, 200.0)])
+def test_layout_model_is_a_partition(n1, n3, L1, L3):
+    """The record model the tests compare with: every bin in exactly one record,
+    at most 4 member slots per record, at most two |k| per record (one per
+    half), and whole records (one |k| each) on square grids of 384^2 and more."""
+    records, halves = grid_records(n1, n3, L1, L3)
+    nh = n1 // 2 + 1
+    slots = {}
+    key = {}
+    for k, cls in enumerate(_classes(n1, n3, L1, L3)):
+        for flat, s_ in cls:
+            slots[flat] = s_
+            key[flat] = k
+    seen = [b for rec in records for b in rec]
+    assert sorted(seen) == list(range(n3 * nh))
+    for rec in records:
+        assert sum(slots[b] for b in rec) <= 4
+        assert len({key[b] for b in rec}) <= (2 if halves else 1)
+    assert halves == (n1 != 384)
