@@ -29,7 +29,7 @@ def _case(n1=16, n2=4, n3=16):
                 n_cut=31, mu_s=np.full((n3, n1), 0.677), tau0=tau0, mu_k=0.525, sigma0=120e6)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 2e-2)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_dc_gradient_matches_oracle(precision, tol):
     from paper_2102_08756_gb300.autograd import hybrid_rupture
     c = _case()
@@ -54,7 +54,7 @@ def test_dc_gradient_matches_oracle(precision, tol):
           f"{np.abs(out.detach().double().cpu().numpy() - taus).max() / np.abs(taus).max():.3e} "
           f"of the peak")
     np.testing.assert_allclose(out.detach().double().cpu().numpy(), taus, rtol=0,
-                               atol=(1e-7 if precision == "fp64" else 5e-3) * np.abs(taus).max())
+                               atol=(1e-10 if precision == "fp64" else 1e-4) * np.abs(taus).max())
     assert abs(float(g) - ref.sum()) < tol * abs(ref.sum()), (float(g), ref.sum())
 
 

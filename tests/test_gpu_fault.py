@@ -2,14 +2,16 @@
 oracle (oracle/fault_oracle.py), through the C ABI; and the paper's TPV3 check
 (Section 3): the hybrid FEM-SBIM run agrees with the SBIM-only run.
 
-Bounds: FP64 1e-8 of the field maximum (slip rate, slip, traction) over a
-nucleating rupture; FP32 (Kahan-summed float history) 3e-3 (stick/slip
-switches amplify the float rounding of the traction near the strength)."""
+Bounds, relative to each field's peak over the run (slip rate, slip, traction)
+of a nucleating rupture: FP64 1e-10; FP32 (Kahan-summed float history) 1e-4.
+The stick/slip decision is a threshold, so a node that changed regime one step
+off would carry an O(1) local error; in these runs no node does (asserted), and
+the FP32 slip rate stays within 1e-5 of its peak (measured)."""
 import numpy as np
 import pytest
 
 from oracle.fault_oracle import FaultLaw, PureSBIMOracle
-from tests._errors import Worst, assert_finite, max_abs_rel
+from tests._errors import assert_finite, max_abs_rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,7 +44,7 @@ def _solver(n1, n3, n_cut, fl, precision, symmetric):
     return g
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 3e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 @pytest.mark.parametrize("symmetric", [False, True])
 @pytest.mark.parametrize("n1,n3,n_cut", [(24, 16, 50), (20, 20, 13)])
 def test_rupture_matches_oracle(precision, tol, symmetric, n1, n3, n_cut):
@@ -50,24 +52,24 @@ def test_rupture_matches_oracle(precision, tol, symmetric, n1, n3, n_cut):
     fl = _law(n1, n3, 3.5, 0.05)
     o = PureSBIMOracle(n1, n3, n1 * DX, n3 * DX, CS, CP, RHO, DT, n_cut, fl, symmetric=symmetric)
     g = _solver(n1, n3, n_cut, fl, precision, symmetric)
-    worst = {"rate": Worst(), "slip": Worst(), "traction": Worst()}
-    peak = 0.0
-    rates, refs = [], []
+    got, ref = {"rate": [], "slip": [], "traction": []}, {"rate": [], "slip": [], "traction": []}
     for _ in range(steps):
         o.step()
         g.step()
         slip, rate, trac = (x.double().cpu().numpy() for x in g.fault_fields())
-        rates.append(rate)
-        refs.append(o.slip_rate.copy())
-        for name, got, ref in (("rate", rate, o.slip_rate), ("slip", slip, o.slip),
-                               ("traction", trac, o.fault_traction)):
-            worst[name].update(max_abs_rel(got, ref, max(np.abs(ref).max(), 1e-30)))
-        peak = max(peak, np.abs(o.slip_rate).max())
-    from tests.test_gpu_hybrid import regime_report
+        for name, x, r in (("rate", rate, o.slip_rate), ("slip", slip, o.slip),
+                           ("traction", trac, o.fault_traction)):
+            got[name].append(assert_finite(x, name))
+            ref[name].append(np.array(r, copy=True))
+    worst = {name: max_abs_rel(np.array(got[name]), np.array(ref[name])) for name in got}
+    peak = np.abs(np.array(ref["rate"])).max()
+    from tests.test_gpu_hybrid import regime_report, regime_stats
     print("\n" + regime_report(f"RUPTURE-REPORT sbim {precision} sym={symmetric} {n1}x{n3}",
-                                rates, refs))
+                                got["rate"], ref["rate"])
+          + f"; slip {worst['slip']:.3e}, traction {worst['traction']:.3e} of their peaks")
     assert peak > 1.0, peak                         # the rupture runs
-    assert all(w.value < tol for w in worst.values()), worst
+    assert regime_stats(got["rate"], ref["rate"])[0] == 0
+    assert all(w < tol for w in worst.values()), worst
     u, v = (x.double().cpu().numpy() for x in g.get_state())
     assert_finite(v, "v")
     assert max_abs_rel(u, o.u) < tol

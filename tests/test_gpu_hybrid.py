@@ -23,12 +23,13 @@ def built():
 rel = rel_l2_field
 
 
-def regime_report(title, rates, refs, thr=1e-3):
-    """Where a lower-precision rupture departs from the FP64 one: the nodes that
-    slip (|slip rate| > thr m/s) at some step in one run but not the other, and
-    the slip-rate error inside and outside that set (max over steps, relative to
-    the FP64 peak)."""
+def regime_stats(rates, refs, thr=1e-3):
+    """Where a lower-precision rupture departs from the FP64 one: the number of
+    nodes that slip (|slip rate| > thr m/s) at some step in one run but not in
+    the other, and the slip-rate error (max over steps and nodes, relative to the
+    FP64 peak) inside and outside that set of nodes."""
     rates, refs = np.array(rates), np.array(refs)
+    assert_finite(rates, "slip rate")
     mag = lambda x: np.sqrt((x ** 2).sum(axis=1))           # noqa: E731  (steps, n3, n1)
     a, b = mag(rates) > thr, mag(refs) > thr
     switch = (a != b).any(axis=0)
@@ -36,16 +37,23 @@ def regime_report(title, rates, refs, thr=1e-3):
     d = np.abs(rates - refs).max(axis=(0, 1))
     inside = d[switch].max() / peak if switch.any() else 0.0
     outside = d[~switch].max() / peak if (~switch).any() else 0.0
-    return (f"{title}: {int(switch.sum())} of {switch.size} nodes change regime at another step; "
+    return int(switch.sum()), switch.size, inside, outside, d.max() / peak, peak
+
+
+def regime_report(title, rates, refs, thr=1e-3):
+    n, total, inside, outside, overall, peak = regime_stats(rates, refs, thr)
+    return (f"{title}: {n} of {total} nodes change regime at another step; "
             f"slip-rate error inside {inside:.3e}, outside {outside:.3e}, overall "
-            f"{d.max() / peak:.3e} of the peak {peak:.3f} m/s")
+            f"{overall:.3e} of the peak {peak:.3f} m/s")
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 5e-6)])
 @pytest.mark.parametrize("fault,boundaries", [(False, True), (True, True), (True, False)])
 def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
     """Random initial state, SBIM or free boundaries, welded split plane or none:
-    u, v, a after 30 steps equal the oracle's."""
+    u, v, a after 30 steps equal the oracle's, each within one bound (the map is
+    linear, so float rounding stays at its own level: measured 4e-7 to 6e-7 in
+    FP32 and 1e-12 in FP64 for all three fields)."""
     from paper_2102_08756_gb300.hybrid import Hybrid
     n1, n2, n3, h, n_cut, steps = 8, 4, 6, 50.0, 12, 30
     dt = 0.3 * h / CP
@@ -68,8 +76,8 @@ def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
     print(f"\nSLAB-REPORT {precision} fault={fault} sbim={boundaries}: relative L2 error "
           f"u {rel(u, o.u):.3e} v {rel(v, o.v):.3e} a {rel(a, o.a):.3e}")
     assert rel(u, o.u) < tol
-    assert rel(v, o.v) < tol * 10
-    assert rel(a, o.a) < tol * 10
+    assert rel(v, o.v) < tol
+    assert rel(a, o.a) < tol
     g.close()
 
 
@@ -81,10 +89,16 @@ def _rupture_setup(n1, n3):
     return mu_s, tau0
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 3e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 def test_rupture_matches_oracle(precision, tol):
     """Slip-weakening rupture from an overstressed patch (TPV3-like stresses,
-    Dc scaled to the small fault): the slip-rate field over 45 steps."""
+    Dc scaled to the small fault): the slip-rate field over 45 steps, within
+    `tol` of the FP64 oracle's peak slip rate at every node and step.  The stick
+    or slip decision of the fault law is a threshold, so a node whose FP32
+    traction crossed the strength one step off would carry an O(1) local error;
+    no node does here (every node slips or sticks at the same steps as in the
+    oracle), and the FP32 error stays at the float rounding of the coupled
+    update (measured 3.4e-6 of the peak)."""
     from paper_2102_08756_gb300.hybrid import Hybrid
     n1 = n3 = 32
     n2, h, steps = 4, 100.0, 45
@@ -109,8 +123,10 @@ def test_rupture_matches_oracle(precision, tol):
         if np.linalg.norm(o.slip_rate) > 0:
             worst.update(rel(rate, o.slip_rate))
     print("\n" + regime_report(f"RUPTURE-REPORT hybrid {precision}", rates, refs))
+    switched, _, _, _, overall, _ = regime_stats(rates, refs)
     assert peak > 1.0
-    assert worst.value < tol, worst
+    assert switched == 0
+    assert overall < tol, overall
     g.close()
 
 
@@ -208,6 +224,8 @@ def test_coupled_configuration_fp32_against_fp64_and_mirror_symmetry():
         g.close()
     r64, top, bot, trac = runs["fp64"]
     r32 = runs["fp32"][0]
+    print("\n" + regime_report("RUPTURE-REPORT coupled 512x16x512 fp32 vs fp64",
+                                list(r32.cpu().numpy()), list(r64.cpu().numpy())))
     assert float(r64.abs().max()) > 1.0                          # the rupture runs
     assert float((r32 - r64).abs().max()) < 3e-3 * float(r64.abs().max())
     scale = float(top.abs().max())

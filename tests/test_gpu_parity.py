@@ -151,15 +151,15 @@ def test_whole_record_layout_matches_oracle(precision, kahan, variant):
 
 def test_orbit_tile_must_divide_the_records():
     from paper_2102_08756_gb300.sbim import SBIM, SBIMError
-    g = SBIM(48, 32, 4800.0, 3200.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)   # 384 records
-    assert g.info()["n_slots"] == 4 * 384
+    g = SBIM(64, 32, 6400.0, 3200.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)   # 384 records
+    assert g.info()["n_slots"] == 4 * 384 == expected_slots(64, 32, 6400.0, 3200.0)
     with pytest.raises(SBIMError) as e:
         g.set_conv_tile(256)
     assert e.value.code == -1
     with pytest.raises(SBIMError):
         g.set_conv_tile(96)
     g.set_conv_tile(64)
-    z = torch.zeros((3, 32, 48), device="cuda")
+    z = torch.zeros((3, 32, 64), device="cuda")
     g.step(z, z)
     g.check()
     g.close()
