@@ -95,6 +95,9 @@ def parse():
     p.add_argument("--tune", action="store_true",
                    help="autotune the convolution launch after the history is filled")
     p.add_argument("--n", type=int, default=None, help="grid size (default 1024)")
+    p.add_argument("--n3", type=int, default=None,
+                   help="grid points along x3 (default: as --n; a rectangular plane)")
+    p.add_argument("--dx", type=float, default=None, help="grid spacing in m (default 100)")
     p.add_argument("--n-cut", type=int, default=None, help="history cutoff (default 4096)")
     p.add_argument("--workload", default="sbim",
                    choices=["sbim", "adjoint-sbim", "coupled", "ensemble", "adjoint", "tpv3"],
@@ -110,8 +113,11 @@ def parse():
 
 def workload(args):
     c = config_large()
-    if args.n:
-        c.update(n1=args.n, n3=args.n, L1=args.n * 100.0, L3=args.n * 100.0)
+    n1 = args.n or c["n1"]
+    n3 = getattr(args, "n3", None) or n1
+    dx = getattr(args, "dx", None) or 100.0
+    if (n1, n3, dx) != (c["n1"], c["n3"], 100.0):
+        c.update(n1=n1, n3=n3, L1=n1 * dx, L3=n3 * dx, dt=0.3 * dx / c["cp"])
     if args.n_cut:
         c["n_cut"] = args.n_cut
     return c
@@ -120,7 +126,7 @@ def workload(args):
 def workload_name(c, precision, kahan, adjoint=False):
     head = ("adjoint SBIM step (transpose of the update, reverse time)" if adjoint
             else "single half-space SBIM step")
-    return (f"{head}, {c['n1']}x{c['n3']} boundary, dx=100 m, "
+    return (f"{head}, {c['n1']}x{c['n3']} boundary, dx={c['L1'] / c['n1']:g} m, "
             f"{c['n_cut']}-lag history, {precision} history"
             + (" + Kahan accumulation" if kahan and precision != "fp64" else ""))
 
@@ -680,6 +686,9 @@ def run_coupled(args):
     for _ in range(n_cut + W):
         g.step()
     torch.cuda.synchronize()
+    from paper_2102_08756_gb300 import sbim as B
+    top = B.sbim_hybrid_info(g.h)[2]
+    B.sbim_set_profiling(top, True)            # stage events of the top half-space
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -693,9 +702,14 @@ def run_coupled(args):
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
+    stage, nprof = B.sbim_stage_times(top)
+    B.sbim_set_profiling(top, False)
     slip, rate, _ = g.fault_fields()
     modes = n3 * (n1 // 2 + 1)
     macs = 2 * modes * n_cut * MACS_PER_PAIR
+    conv_ms = stage["convolution"] / nprof
+    alg = (modes * n_cut + modes) * BYTES_PER_PAIR["fp32"]
+    peak, peak_kind = peaks()
     line = {
         "metric": "coupled hybrid steps/s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
         "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -704,6 +718,12 @@ def run_coupled(args):
                                f"slip-weakening fault, two SBIM half-spaces, {n_cut}-lag history",
                    "elements": n1 * n2 * n3, "l2": "history (12.6 GB) >> L2"},
         "sbim_macs_per_s": macs / (ms * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": alg / (conv_ms * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (conv_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                     "kernel": "conv_tma_kernel (one half-space's launch, its stage events)",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                     "launch_ms": conv_ms},
+        "stage_ms_per_step_top": {k: v / nprof for k, v in stage.items()},
         "fault": {"max_slip_m": float(slip.abs().max()), "max_slip_rate_m_s": float(rate.abs().max()),
                   "simulated_s": (n_cut + W + K) * dt},
         "clocks": clk.summary(),
@@ -753,6 +773,12 @@ def run_tpv3(args):
             arrival = torch.where((mag > 1e-3) & torch.isinf(arrival), float(m + 1) * dt, arrival)
         torch.cuda.synchronize()
         K = args.steps
+        # the pure-SBIM solver's upper half-space: its stage events time the one
+        # history pass of each step (the step's convolution and its corrector's
+        # lag-0 re-evaluation)
+        up = g.handles()[0] if hasattr(g, "handles") else None
+        if up is not None:
+            B.sbim_set_profiling(up, True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
@@ -761,15 +787,25 @@ def run_tpv3(args):
                 g.step()
             e1.record()
             torch.cuda.synchronize()
-        out = (arrival.cpu().numpy(), mag.cpu().numpy(), e0.elapsed_time(e1) / K, clk.summary())
+        conv = None
+        if up is not None:
+            stage, _ = B.sbim_stage_times(up)
+            B.sbim_set_profiling(up, False)
+            conv = stage["convolution"] / K
+        out = (arrival.cpu().numpy(), mag.cpu().numpy(), e0.elapsed_time(e1) / K, clk.summary(), conv)
         g.close()
         return out
 
-    t_h, s_h, ms_h, clk_h = solve(lambda: Hybrid(n1, TPV3["strip_cells"], n3, h, cs, cp, rho, dt,
-                                                 steps, "fp32"))
+    from paper_2102_08756_gb300 import sbim as B
+    t_h, s_h, ms_h, clk_h, _ = solve(lambda: Hybrid(n1, TPV3["strip_cells"], n3, h, cs, cp, rho,
+                                                    dt, steps, "fp32"))
     torch.cuda.empty_cache()
-    t_p, s_p, ms_p, clk_p = solve(lambda: FaultSolver(n1, n3, n1 * h, n3 * h, cs, cp, rho, dt,
-                                                      steps, "fp32", True))
+    t_p, s_p, ms_p, clk_p, conv_p = solve(lambda: FaultSolver(n1, n3, n1 * h, n3 * h, cs, cp, rho,
+                                                              dt, steps, "fp32", True))
+    modes = n3 * (n1 // 2 + 1)
+    alg = (modes * steps + modes) * BYTES_PER_PAIR["fp32"]
+    peak, peak_kind = peaks()
+    slots = B.sbim_plan(n1, n3, n1 * h, n3 * h, steps, "fp32")["n_slots"]
     both = np.isfinite(t_h) & np.isfinite(t_p)
     either = np.isfinite(t_h) | np.isfinite(t_p)
     line = {
@@ -781,6 +817,12 @@ def run_tpv3(args):
                                f"(symmetry plane) vs hybrid with a 4-element slab",
                    "l2": "history >> L2"},
         "hybrid_ms_per_step": ms_h,
+        "roofline": {"bound": "hbm", "achieved": alg / (conv_p * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (conv_p * 1e-3) / 1e9 / peak, "traffic": None,
+                     "kernel": "conv_tma_kernel + repeat_lag0_kernel (the step's one history pass)",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                     "launch_ms": conv_p},
+        "layout": {"modes": modes, "slots": slots, "padding": slots / modes},
         "agreement": {
             "ruptured_nodes": int(both.sum()), "ruptured_either": int(either.sum()),
             "arrival_rms_s": float(np.sqrt(np.mean((t_h[both] - t_p[both]) ** 2))),
@@ -873,6 +915,13 @@ def run_ensemble(args):
                                "hybrid batch replayed from a CUDA graph",
                    "history_bytes": hist_bytes, "l2": "history >> L2"},
         "sbim_macs_per_s": macs / (ms * 1e-3), "hbm_gbs_history": hist_bytes / (ms * 1e-3) / 1e9,
+        # the batched convolution runs inside the replayed graph, so only the
+        # whole step is timed: a lower bound on the convolution's own rate
+        "roofline": {"bound": "hbm", "achieved": hist_bytes / (ms * 1e-3) / 1e9, "peak": peaks()[0],
+                     "unit": "GB/s", "frac": hist_bytes / (ms * 1e-3) / 1e9 / peaks()[0],
+                     "traffic": None, "peak_kind": peaks()[1],
+                     "kernel": "whole ensemble step (graph replay, FE stages included)",
+                     "algorithmic_bytes_per_launch": hist_bytes, "launch_ms": ms},
         "max_slip_rate_m_s": peak_rate, "clocks": clk.summary(),
     }
     if tuned is not None:
