@@ -328,15 +328,22 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
   if (have_left) emit(left, Half{{pad, pad}, 0.0});
 }
 
-// The record layout of a grid: whole records unless they would pad the
-// history by more than 3 % over the bins (rectangular planes), where half
-// records take their place.  Returns whether the layout has half records.
+// The record layout of a grid: whole records unless half records would store
+// more than 12 % less history.  The half-record kernels stream their bytes
+// ~13 % slower (a second weight set per record and lag; on GB300 0.935 against
+// 1.07 of the copy bandwidth), so they pay only where whole records are mostly
+// padding: rectangular planes (the TPV3 plane: 1.20x the bins as whole records,
+// 1.006x as half records) and a few tiny grids; squares of 32^2 and more keep
+// whole records.  Returns whether the layout has half records.
 bool plan_layout(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half) {
   plan_orbits(c, mem, q_half, false);
   if ((double)mem.size() <= 1.03 * c.nbins) return false;
-  mem.clear();
-  q_half.clear();
-  plan_orbits(c, mem, q_half, true);
+  std::vector<Member> mem_h;
+  std::vector<double> q_h;
+  plan_orbits(c, mem_h, q_h, true);
+  if ((double)mem.size() <= 1.12 * (double)mem_h.size()) return false;
+  mem.swap(mem_h);
+  q_half.swap(q_h);
   return true;
 }
 

@@ -93,12 +93,15 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 // (hides their L2 latency, at KS x 16 floats of registers per thread).  The
 // compensated BF16 kernels, whose unpacked records and Kahan terms already
 // fill the register file, interpolate each stage's weights in place instead.
-// Half-record kernels (whose second weight set takes the registers) interpolate
-// in place too.
-template <class S, int KAHAN, bool HALVES> struct PrefetchNodes {
-  static constexpr bool value = !HALVES;
+// Half-record kernels prefetch the nodes of both halves where the register
+// budget allows it (<= 2 resident CTAs per 128 records, <= 2 lags per stage,
+// float history) and interpolate in place otherwise.
+template <class S, int KAHAN, bool HALVES, int NS, int KS, int MINB, int TILE> struct PrefetchNodes {
+  static constexpr bool value =
+      !HALVES || (KS <= 2 && MINB * TILE <= 2 * 128 && sizeof(typename S::real) == 4);
 };
-template <bool LO, bool HALVES> struct PrefetchNodes<dev::StoreBF16<LO>, 1, HALVES> {
+template <bool LO, bool HALVES, int NS, int KS, int MINB, int TILE>
+struct PrefetchNodes<dev::StoreBF16<LO>, 1, HALVES, NS, KS, MINB, TILE> {
   static constexpr bool value = false;
 };
 
@@ -156,7 +159,7 @@ __device__ __forceinline__ void interp_nodes(const T4 nd[4], unsigned long long 
 // over from item to item through the running stage count `gstage` (stage s of
 // this item is global stage gstage + s: buffer (gstage + s) % NS, parity
 // ((gstage + s) / NS) & 1).  Returns false if a bounded wait gave up.
-template <class S, int KAHAN, int NS, int KS, int TILE, bool HALVES>
+template <class S, int KAHAN, int NS, int KS, int MINB, int TILE, bool HALVES>
 __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int chunk,
                                               unsigned char* smem, unsigned long long* full,
                                               unsigned& gstage) {
@@ -289,9 +292,11 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
     if (tid == 0)
       for (int s = 0; s < min(NS - 1, nst); ++s) issue(s);
 
-    constexpr bool PF = PrefetchNodes<S, KAHAN, HALVES>::value;
+    constexpr bool PF = PrefetchNodes<S, KAHAN, HALVES, NS, KS, MINB, TILE>::value;
+    constexpr bool HP = PF && HALVES;   // half 1's nodes prefetched as well
     // weights of stage 0 (prefetching shapes)
     R wn[KS][4];
+    R wn1[HP ? KS : 1][4];
     if constexpr (PF) if (!pre) {
       T4 nd[KS][4];
 #pragma unroll
@@ -303,6 +308,19 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           interp_nodes(nd[k], (unsigned long long)(mf + k) * us, dT, wn[k]);
         } else {
           wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
+        }
+      }
+      if constexpr (HP) if (!same) {
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          if (mf + k < m1) fetch_nodes(tab, (unsigned long long)(mf + k) * us1, nd[k]);
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (mf + k < m1 && mf + k < lo1) {
+            interp_nodes(nd[k], (unsigned long long)(mf + k) * us1, dT1, wn1[k]);
+          } else {
+            wn1[k][0] = wn1[k][1] = wn1[k][2] = wn1[k][3] = (R)0;
+          }
         }
       }
     }
@@ -329,6 +347,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       // table nodes of the next stage, in flight during this stage's arithmetic
       const int mn = mb + KS;
       T4 nd[PF ? KS : 1][4];
+      T4 nd1[HP ? KS : 1][4];
       if constexpr (WSEG > 0) if (pre) {
         // precomputed weights from the stage; the two 16-byte halves are read in
         // an order that keeps a quarter warp on distinct bank groups
@@ -369,15 +388,27 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       // half 1's weights: half 0's when the record holds one |k|, else
       // interpolated here (half 0's are prefetched, precomputed or in place)
       R w1[KS][4];
+      if (same) {
 #pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        if (same) {
+        for (int k = 0; k < KS; ++k)
 #pragma unroll
           for (int q = 0; q < 4; ++q) w1[k][q] = w[k][q];
-        } else if (mb + k < m1 && mb + k < lo1) {
-          lag_weights(tab, (unsigned long long)(mb + k) * us1, dT1, w1[k]);
-        } else {
-          w1[k][0] = w1[k][1] = w1[k][2] = w1[k][3] = (R)0;
+      } else if constexpr (HP) {
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w1[k][q] = wn1[k][q];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          if (mn + k < m1) fetch_nodes(tab, (unsigned long long)(mn + k) * us1, nd1[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (mb + k < m1 && mb + k < lo1) {
+            lag_weights(tab, (unsigned long long)(mb + k) * us1, dT1, w1[k]);
+          } else {
+            w1[k][0] = w1[k][1] = w1[k][2] = w1[k][3] = (R)0;
+          }
         }
       }
 
@@ -474,6 +505,16 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
             wn[k][0] = wn[k][1] = wn[k][2] = wn[k][3] = (R)0;
           }
         }
+        if constexpr (HP) if (!same) {
+#pragma unroll
+          for (int k = 0; k < KS; ++k) {
+            if (mn + k < m1 && mn + k < lo1) {
+              interp_nodes(nd1[k], (unsigned long long)(mn + k) * us1, dT1, wn1[k]);
+            } else {
+              wn1[k][0] = wn1[k][1] = wn1[k][2] = wn1[k][3] = (R)0;
+            }
+          }
+        }
       }
     }
     if (!ok) {
@@ -518,7 +559,7 @@ __global__ void __launch_bounds__(TILE, MINB) conv_tma_kernel(const StepArgs a) 
   __shared__ __align__(8) unsigned long long full[NS];
   init_barriers<NS>(full);
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, MINB, TILE, HALVES>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
 }
 
 // Persistent CTAs over the (update, tile, chunk) items of a batch of updates
@@ -554,7 +595,7 @@ conv_tma_batch_kernel(const StepArgs* __restrict__ args, const int* __restrict__
     }
     __syncthreads();
     if (s_item >= total) break;
-    if (!conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage))
+    if (!conv_tma_item<S, KAHAN, NS, KS, MINB, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage))
       return;
   }
 }
@@ -583,7 +624,7 @@ conv_tma_items_kernel(const StepArgs* __restrict__ args, const int* __restrict__
   }
   init_barriers<NS>(full);   // its __syncthreads publishes the item too
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, MINB, TILE, HALVES>(s_args, s_tile, s_chunk, smem, full, gstage);
 }
 
 // Launch one instantiation (sets the dynamic shared-memory attribute once).

@@ -12,7 +12,9 @@ of L1 and L3) and ordered by (|k|^2, j1, r3).  A bin contributes 1 member slot,
   record, other bins two to a half); a class's halves pair up into records and
   an odd leftover half pairs with the next class's leftover.
 
-A grid uses whole records unless they would exceed 1.03 x the bins in slots.
+A grid uses whole records unless they exceed 1.03 x the bins in slots and
+1.12 x the slots of the half records (the half-record kernels stream their
+bytes ~13 % slower, so half records must save more than that).
 """
 from fractions import Fraction
 
@@ -84,7 +86,10 @@ def grid_records(n1, n3, L1, L3):
     whole = _whole(classes)
     if 4 * len(whole) <= 1.03 * n3 * (n1 // 2 + 1):
         return whole, False
-    return _halves(classes), True
+    halves = _halves(classes)
+    if len(whole) <= 1.12 * len(halves):
+        return whole, False
+    return halves, True
 
 
 def expected_slots(n1, n3, L1, L3, tile=128):

@@ -135,10 +135,9 @@ def test_orbit_tiles_match_oracle(precision, kahan, tile, variant):
 @pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("bf16x2", 1), ("fp32", 0)])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_whole_record_layout_matches_oracle(precision, kahan, variant):
-    """384 x 384: the smallest square grid whose whole-record layout (every
-    record one class of equal |k|) pads under 3 %, so it runs the whole-record
-    kernels that the benchmark grids use; every mode, ring wrap-around, both
-    half-spaces, against the oracle."""
+    """384 x 384 in the whole-record layout (every record one class of equal
+    |k|, 1.02x the bins) that the benchmark grids use; every mode, ring
+    wrap-around, both half-spaces, against the oracle."""
     from tests._layout import grid_records
     n, dx = 384, 100.0
     records, halves = grid_records(n, n, n * dx, n * dx)
@@ -570,7 +569,9 @@ def test_rectangular_orbits_group_equal_wavenumbers(grid):
     fraction, grouped in floating point), so the history carries no more
     padding than the classes force; parity over several orbit tiles."""
     from paper_2102_08756_gb300.sbim import SBIM, sbim_plan
+    from tests._layout import grid_records
     n1, n3, L1, L3 = grid
+    assert grid_records(n1, n3, L1, L3)[1]          # the half-record layout
     g = SBIM(n1, n3, L1, L3, CS, CP, RHO, 0.3 * (L1 / n1) / CP, 8, 1, "fp32", 1)
     info = g.info()
     assert info["n_slots"] == expected_slots(n1, n3, L1, L3)

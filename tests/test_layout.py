@@ -71,7 +71,8 @@ def test_plan_rejects_bad_arguments(plan, args):
 def test_layout_model_is_a_partition(n1, n3, L1, L3):
     """The record model the tests compare with: every bin in exactly one record,
     at most 4 member slots per record, at most two |k| per record (one per
-    half), and whole records (one |k| each) on square grids of 384^2 and more."""
+    half), whole records (one |k| each) on the square grids and half records on
+    the rectangular planes."""
     records, halves = grid_records(n1, n3, L1, L3)
     nh = n1 // 2 + 1
     slots = {}
@@ -85,4 +86,4 @@ def test_layout_model_is_a_partition(n1, n3, L1, L3):
     for rec in records:
         assert sum(slots[b] for b in rec) <= 4
         assert len({key[b] for b in rec}) <= (2 if halves else 1)
-    assert halves == (n1 != 384)
+    assert halves == (n1 != n3 and L1 != L3)
