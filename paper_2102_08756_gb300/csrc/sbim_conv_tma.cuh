@@ -223,11 +223,13 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
     }
     R w0[4], w1[4];
     lag_weights(tab, 0ull, dT * (R)0.5, w0);
-    if (same) {
+    if constexpr (HALVES) {
+      if (same) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) w1[q] = w0[q];
-    } else {
-      lag_weights(tab, 0ull, dT1 * (R)0.5, w1);
+        for (int q = 0; q < 4; ++q) w1[q] = w0[q];
+      } else {
+        lag_weights(tab, 0ull, dT1 * (R)0.5, w1);
+      }
     }
     C Dp[3][4];
 #pragma unroll
@@ -239,6 +241,9 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
           for (int c = 0; c < 3; ++c) Dp[c][j] = D[c][((j / MPC + r) % NCH) * MPC + j % MPC];
         }
     // slot j holds member ((j / MPC + rot) % NCH) MPC + j % MPC, of half member / 2
+    if constexpr (!HALVES) {
+      accumulate<KAHAN>(acc, cmp, w0, w0, Dp);
+    } else
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const bool h1 = ((j / MPC + rot) % NCH) * MPC + j % MPC >= 2;
@@ -388,7 +393,8 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
       // half 1's weights: half 0's when the record holds one |k|, else
       // interpolated here (half 0's are prefetched, precomputed or in place)
       R w1[KS][4];
-      if (same) {
+      if constexpr (!HALVES) {
+      } else if (same) {
 #pragma unroll
         for (int k = 0; k < KS; ++k)
 #pragma unroll
@@ -419,7 +425,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
         // a chunk of <= 2 members lies in one half (ch MPC / 2); a 4-member
         // chunk spans both, selected per member below
         R wc[KS][4];
-        if constexpr (MPC <= 2) {
+        if constexpr (MPC <= 2 && HALVES) {
           const bool h1 = ch * MPC >= 2;
 #pragma unroll
           for (int k = 0; k < KS; ++k)
@@ -456,7 +462,8 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
 #pragma unroll
               for (int k = 0; k < KS; ++k) {
                 R wk;
-                if constexpr (MPC <= 2) wk = wc[k][kern[f]];
+                if constexpr (!HALVES) wk = w[k][kern[f]];
+                else if constexpr (MPC <= 2) wk = wc[k][kern[f]];
                 else wk = j < 2 ? w[k][kern[f]] : w1[k][kern[f]];
                 y = fma2(make_float2(wk, wk), D[k][comp[f]][j], y);
               }
@@ -481,7 +488,8 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
               for (int k = 0; k < KS; ++k) {
                 const C d = D[k][comp[f]][j];
                 R wk;
-                if constexpr (MPC <= 2) wk = wc[k][kern[f]];
+                if constexpr (!HALVES) wk = w[k][kern[f]];
+                else if constexpr (MPC <= 2) wk = wc[k][kern[f]];
                 else wk = j < 2 ? w[k][kern[f]] : w1[k][kern[f]];
                 y = fma(wk, (f & 1) ? d.y : d.x, y);
               }
