@@ -108,7 +108,6 @@ struct sbim_ctx {
   int variant = 1;            // 0: register-prefetch loads, 1-3: TMA-staged history shapes
   int tile = sbim::kOrbitTile;  // orbits per CTA of the TMA convolution: 64, 128 or 256
   bool halves = false;        // records may hold two |k| (half-record layout)
-  int n_same = 0;             // records [0, n_same) hold one |k| (all of them unless halves)
   int lags_per_cta = 0;       // 0: automatic
   size_t part_bytes = 0;
   double tab_h = 0;
@@ -203,7 +202,7 @@ long long history_record_bytes(int prec) {
 //     rectangular planes, where most classes are pairs {(j1, j3), (j1, -j3)}
 //     and whole records would be half empty.
 void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half,
-                 bool halves, int* n_same = nullptr) {
+                 bool halves) {
   long long ra, rb;
   period_ratio(c, ra, rb);
   const bool exact = ra > 0;
@@ -246,18 +245,13 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
     Member m[2];
     double q;
   };
-  // half-record layouts: the records of one |k| first, the mixed ones after
-  std::vector<Member> mix_mem;
-  std::vector<double> mix_q;
   auto emit = [&](const Half& x, const Half& y) {
-    std::vector<Member>& mm = x.q == y.q ? mem : mix_mem;
-    std::vector<double>& qq = x.q == y.q ? q_half : mix_q;
-    mm.push_back(x.m[0]);
-    mm.push_back(x.m[1]);
-    mm.push_back(y.m[0]);
-    mm.push_back(y.m[1]);
-    qq.push_back(x.q);
-    qq.push_back(y.q);
+    mem.push_back(x.m[0]);
+    mem.push_back(x.m[1]);
+    mem.push_back(y.m[0]);
+    mem.push_back(y.m[1]);
+    q_half.push_back(x.q);
+    q_half.push_back(y.q);
   };
   std::vector<Member> cur;
   auto flush_whole = [&](double q) {
@@ -332,26 +326,6 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
     i = j;
   }
   if (have_left) emit(left, Half{{pad, pad}, 0.0});
-  // Where it costs at most 5 % of the records, the records of one |k| are padded
-  // to a multiple of the 128-record tile so that the convolution runs them with
-  // the whole-record kernel (~13 % faster) and only the mixed ones with the
-  // half-record kernel; otherwise (small grids) every record takes the
-  // half-record kernel.
-  int same_n = (int)(q_half.size() / 2);
-  if (halves && !mix_q.empty()) {
-    const int mix_n = (int)(mix_q.size() / 2);
-    const int fill = (sbim::kOrbitTile - same_n % sbim::kOrbitTile) % sbim::kOrbitTile;
-    const bool split = 20 * fill <= same_n + mix_n;
-    if (split) {
-      same_n += fill;
-      mem.resize((size_t)same_n * 4, pad);
-      q_half.resize((size_t)same_n * 2, 0.0);
-    }
-    mem.insert(mem.end(), mix_mem.begin(), mix_mem.end());
-    q_half.insert(q_half.end(), mix_q.begin(), mix_q.end());
-    if (!split) same_n = 0;
-  }
-  if (n_same) *n_same = same_n;
 }
 
 // The record layout of a grid: whole records unless half records would store
@@ -361,19 +335,15 @@ void plan_orbits(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double
 // padding: rectangular planes (the TPV3 plane: 1.20x the bins as whole records,
 // 1.006x as half records) and a few tiny grids; squares of 32^2 and more keep
 // whole records.  Returns whether the layout has half records.
-bool plan_layout(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half,
-                 int* n_same = nullptr) {
+bool plan_layout(const sbim_ctx& c, std::vector<Member>& mem, std::vector<double>& q_half) {
   plan_orbits(c, mem, q_half, false);
-  if (n_same) *n_same = (int)(q_half.size() / 2);
   if ((double)mem.size() <= 1.03 * c.nbins) return false;
   std::vector<Member> mem_h;
   std::vector<double> q_h;
-  int same_h = 0;
-  plan_orbits(c, mem_h, q_h, true, &same_h);
+  plan_orbits(c, mem_h, q_h, true);
   if ((double)mem.size() <= 1.12 * (double)mem_h.size()) return false;
   mem.swap(mem_h);
   q_half.swap(q_h);
-  if (n_same) *n_same = same_h;
   return true;
 }
 
@@ -458,11 +428,9 @@ int create_impl(sbim_ctx* c) {
 
   std::vector<Member> mem;
   std::vector<double> q_half;
-  int n_same = 0;
-  c->halves = plan_layout(*c, mem, q_half, &n_same);
+  c->halves = plan_layout(*c, mem, q_half);
   c->n_orb = (int)(q_half.size() / 2);
   c->n_orb_pad = (c->n_orb + sbim::kOrbitTile - 1) / sbim::kOrbitTile * sbim::kOrbitTile;
-  c->n_same = c->halves ? std::min(n_same, c->n_orb_pad) : c->n_orb_pad;
   mem.resize((size_t)c->n_orb_pad * 4, Member{-1, 1.0, 0.0, 0.0f});
   q_half.resize((size_t)c->n_orb_pad * 2, 0.0);
 
@@ -601,9 +569,6 @@ sbim::StepArgs step_args(const sbim_ctx* c) {
   a.fhat = c->d_fhat;
   a.n_orb_pad = c->n_orb_pad;
   a.halves = c->halves ? 1 : 0;
-  a.n_same = c->n_same;
-  a.rec_begin = 0;
-  a.rec_end = c->n_orb_pad;
   a.nbins = c->nbins;
   a.n_cut = c->n_cut;
   a.lc = c->lc;

@@ -51,36 +51,14 @@ static cudaError_t dispatch(const StepArgs& a, int precision, int kahan, int sha
   }
 }
 
-// A half-record layout leads with the records that hold one |k| (n_same of
-// them, a multiple of 128): they run the whole-record kernel, and only the
-// records of two |k| the half-record kernel.  Batches, and tiles that do not
-// divide n_same, run the half-record kernel over every record.
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
                             cudaStream_t st, const BatchLaunch* batch, int tile, bool halves) {
-  if (batch || !halves || a.n_same % tile != 0)
-    return dispatch(a, precision, kahan, shape, st, batch, false, tile, halves);
-  cudaError_t e = cudaSuccess;
-  if (a.n_same > 0) {
-    StepArgs w = a;
-    w.rec_begin = 0;
-    w.rec_end = a.n_same;
-    e = dispatch(w, precision, kahan, shape, st, nullptr, false, tile, false);
-  }
-  if (e == cudaSuccess && a.n_same < a.n_orb_pad) {
-    StepArgs h = a;
-    h.rec_begin = a.n_same;
-    h.rec_end = a.n_orb_pad;
-    e = dispatch(h, precision, kahan, shape, st, nullptr, false, tile, true);
-  }
-  return e;
+  return dispatch(a, precision, kahan, shape, st, batch, false, tile, halves);
 }
 
 cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile, bool halves) {
   const StepArgs none{};
-  cudaError_t e = dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile, false);
-  if (e == cudaSuccess && halves)
-    e = dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile, true);
-  return e;
+  return dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile, halves);
 }
 
 int conv_tma_ctas_per_sm(int precision, int shape, int tile) {

@@ -173,7 +173,7 @@ __device__ __forceinline__ bool conv_tma_item(const StepArgs& a, int tile, int c
   constexpr int MPC = S::kChunkMembers, NCH = S::kChunks;
 
   const int tid = threadIdx.x;
-  const int tile0 = tile * TILE;   // tile counts from record 0 of the update
+  const int tile0 = tile * TILE;
   const int o = tile0 + tid;
   const long long n = *a.step;
   const int n_valid = (n + 1 < (long long)a.n_cut) ? (int)(n + 1) : a.n_cut;
@@ -567,8 +567,7 @@ __global__ void __launch_bounds__(TILE, MINB) conv_tma_kernel(const StepArgs a) 
   __shared__ __align__(8) unsigned long long full[NS];
   init_barriers<NS>(full);
   unsigned gstage = 0;
-  conv_tma_item<S, KAHAN, NS, KS, MINB, TILE, HALVES>(a, a.rec_begin / TILE + blockIdx.x, blockIdx.y,
-                                                      smem, full, gstage);
+  conv_tma_item<S, KAHAN, NS, KS, MINB, TILE, HALVES>(a, blockIdx.x, blockIdx.y, smem, full, gstage);
 }
 
 // Persistent CTAs over the (update, tile, chunk) items of a batch of updates
@@ -672,9 +671,8 @@ cudaError_t launch_shape(const StepArgs& a, cudaStream_t st, const BatchLaunch* 
     conv_tma_batch_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES><<<batch->ctas, TILE, bytes, st>>>(
         batch->args, batch->item_prefix, batch->nb, batch->counter);
   } else {
-    if (a.n_orb_pad % TILE != 0 || a.rec_begin % TILE != 0 || a.rec_end % TILE != 0)
-      return cudaErrorInvalidValue;
-    const dim3 grid((a.rec_end - a.rec_begin) / TILE, a.nchunks);
+    if (a.n_orb_pad % TILE != 0) return cudaErrorInvalidValue;
+    const dim3 grid(a.n_orb_pad / TILE, a.nchunks);
     conv_tma_kernel<S, KAHAN, NS, KS, MINB, TILE, HALVES><<<grid, TILE, bytes, st>>>(a);
   }
   return cudaGetLastError();

@@ -55,9 +55,6 @@ struct StepArgs {
   // sizes (host values)
   int n_orb_pad;
   int halves;                      // 1: a record's two halves may hold different |k|
-  int n_same;                      // half-record layouts: records [0, n_same) hold one |k|
-                                   // (a multiple of 128, or 0), the rest two; else n_orb_pad
-  int rec_begin, rec_end;          // record range of one convolution launch
   int nbins;
   int n_cut;
   int lc;                          // lags per chunk

@@ -10,9 +10,7 @@ of L1 and L3) and ordered by (|k|^2, j1, r3).  A bin contributes 1 member slot,
 * whole records: each class fills records of its own;
 * half records: each class fills halves (a Nyquist bin one half, the corner a
   record, other bins two to a half); a class's halves pair up into records and
-  an odd leftover half pairs with the next class's leftover.  The records of
-  one |k| come first (padded to a multiple of 128 records where that costs at
-  most 5 % of the records), the mixed ones after them.
+  an odd leftover half pairs with the next class's leftover.
 
 A grid uses whole records unless they exceed 1.03 x the bins in slots and
 1.12 x the slots of the half records (the half-record kernels stream their
@@ -58,14 +56,7 @@ def _whole(classes):
 
 
 def _halves(classes):
-    """Half records in the layout's order: the records of one |k| first,
-    padded with empty records to a multiple of 256, then the mixed ones."""
-    same, mixed = [], []
-    records, left = same, None
-
-    def emit(x, y, one_k):
-        (same if one_k else mixed).append(sorted(set(x + y)))
-
+    records, left = [], None
     for cls in classes:
         halves, singles = [], []
         for flat, slots in cls:
@@ -76,42 +67,29 @@ def _halves(classes):
         halves += [singles[k:k + 2] for k in range(0, len(singles), 2)]
         h = 0
         while h + 1 < len(halves):
-            emit(halves[h], halves[h + 1], True)
+            records.append(sorted(set(halves[h] + halves[h + 1])))
             h += 2
         if h < len(halves):
             if left is None:
                 left = halves[h]
             else:
-                emit(left, halves[h], False)
+                records.append(left + halves[h])
                 left = None
     if left is not None:
-        emit(left, [], False)
-    fill = -len(same) % 128
-    split = 0
-    if mixed and 20 * fill <= len(same) + len(mixed):
-        same += [[]] * fill
-        split = len(same)
-    return same + mixed, split
-
-
-def layout(n1, n3, L1, L3):
-    """(records, halves, split): the records as lists of flat bins in layout
-    order, whether they are half records, and the number of leading records of
-    one |k| the whole-record kernel runs (0: none split off)."""
-    classes = _classes(n1, n3, L1, L3)
-    whole = _whole(classes)
-    if 4 * len(whole) <= 1.03 * n3 * (n1 // 2 + 1):
-        return whole, False, 0
-    halves, split = _halves(classes)
-    if len(whole) <= 1.12 * len(halves):
-        return whole, False, 0
-    return halves, True, split
+        records.append(left)
+    return records
 
 
 def grid_records(n1, n3, L1, L3):
     """(records, halves): the records as lists of flat bins, in layout order."""
-    records, halves, _ = layout(n1, n3, L1, L3)
-    return records, halves
+    classes = _classes(n1, n3, L1, L3)
+    whole = _whole(classes)
+    if 4 * len(whole) <= 1.03 * n3 * (n1 // 2 + 1):
+        return whole, False
+    halves = _halves(classes)
+    if len(whole) <= 1.12 * len(halves):
+        return whole, False
+    return halves, True
 
 
 def expected_slots(n1, n3, L1, L3, tile=128):
@@ -125,4 +103,3 @@ def square_grid_records(n, tile=128):
     whole tiles (the layout of a square grid; integer keys j1^2 + j3^2)."""
     records, _ = grid_records(n, n, float(n), float(n))
     return records, -(-len(records) // tile) * tile
-

@@ -148,25 +148,6 @@ def test_whole_record_layout_matches_oracle(precision, kahan, variant):
         assert es < TOL[precision] and et < TOL[precision], (side, es, et)
 
 
-@pytest.mark.parametrize("precision,kahan", [("fp32", 1), ("fp64", 0), ("bf16x2", 1), ("bf16", 0)])
-@pytest.mark.parametrize("variant,tile", [(1, 128), (2, 128), (3, 128), (2, 64)])
-def test_half_record_split_matches_oracle(precision, kahan, variant, tile):
-    """A rectangular plane (192 x 96, L1 / L3 = 2) in the half-record layout
-    whose records of one |k| lead, padded to a tile boundary: the convolution
-    runs them with the whole-record kernel and the mixed records with the
-    half-record kernel, two launches per step.  Every mode against the oracle,
-    with ring wrap-around, both half-spaces and a truncation window."""
-    from tests._layout import layout
-    n1, n3, L1, L3 = 192, 96, 19200.0, 9600.0
-    _, halves, split = layout(n1, n3, L1, L3)
-    assert halves and split == 1792
-    for side, n_cut, window in ((1, 9, 0.0), (-1, 14, 5.1)):
-        es, et = run_parity(n1, n3, L1, L3, n_cut, side, n_cut + 5, precision, kahan,
-                            seed=variant + tile + n_cut, spectrum="k2", variant=variant, tile=tile,
-                            window=window)
-        assert es < TOL[precision] and et < TOL[precision], (side, es, et)
-
-
 def test_orbit_tile_must_divide_the_records():
     from paper_2102_08756_gb300.sbim import SBIM, SBIMError
     g = SBIM(64, 32, 6400.0, 3200.0, CS, CP, RHO, 0.005, 8, 1, "fp32", 1)   # 384 records

@@ -87,12 +87,3 @@ def test_layout_model_is_a_partition(n1, n3, L1, L3):
         assert sum(slots[b] for b in rec) <= 4
         assert len({key[b] for b in rec}) <= (2 if halves else 1)
     assert halves == (n1 != n3 and L1 != L3)
-    if halves:
-        # the records of one |k| lead (padded to a multiple of 128 records where
-        # the padding is at most 5 % of the records)
-        mixed = [i for i, rec in enumerate(records) if len({key[b] for b in rec}) > 1]
-        if mixed:
-            # one contiguous block at the end (a last leftover half, alone with a
-            # padding half, may close it)
-            assert mixed == list(range(mixed[0], mixed[-1] + 1))
-            assert len(records) - 1 - mixed[-1] <= 1
