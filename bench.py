@@ -48,9 +48,13 @@ MACS_PER_PAIR = 5
 DEFAULT_VARIANT = {"fp32": 2, "bf16": 2, "bf16x2": 2, "fp64": 1}
 BYTES_PER_PAIR = {"fp64": 48, "fp32": 24, "bf16x2": 24, "bf16": 12}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per convolution launch measured by ncu, scaled to the
-# full 1024^2 x 4096 workload, valid only for the kernel source with this hash.
-NCU_TRAFFIC = {"conv_src_sha1": "2441d01ed0673ce4b30497592b19f36e58a35381", "bytes_per_launch": 52.159e9 + 183.25e6}
+# DRAM bytes (read + write) per convolution launch of the full 1024^2 x 4096
+# workload, valid only for the kernel source with this hash: ncu's DRAM bytes of
+# one launch at 512^2 x 1024 lags (1.00645 x the ring buffer read, plus the
+# lag-chunk partial sums written), scaled component by component to the full
+# launch's ring buffer (52.043 GB) and its 7 chunks of partial sums.
+NCU_TRAFFIC = {"conv_src_sha1": "d1b3f30aafb73ac2c9a98a81019e7f97f29c7fa2",
+               "bytes_per_launch": 52.3785e9 + 160.9e6}
 
 
 # The TPV3 benchmark as Section 3 states it (material, friction, prestress,
