@@ -261,8 +261,9 @@ int sbim_stage_times(sbim_handle h, double ms[5], long long* steps);
  *   variant       1, 2, 3: history slots staged in shared memory by TMA bulk
  *                 copies, blocked compensated sums; the three pipeline shapes are
  *                 4 stages x 2 lags x 2 CTAs/SM, 3 x 2 x 3, 2 x 4 x 2 (FP32 / BF16
- *                 hi-lo), 8 x 2 x 2, 6 x 2 x 3, 4 x 4 x 2 (BF16 hi-only),
- *                 3 x 1, 4 x 1, 2 x 2 at 2 CTAs/SM (FP64); 0: per-thread register
+ *                 hi-lo), 8 x 2 x 2, 6 x 2 x 3, 4 x 4 x 2 (compensated BF16
+ *                 hi-only), 6 x 1 x 4, 6 x 1 x 5, 6 x 2 x 3 (uncompensated BF16
+ *                 hi-only), 3 x 1, 4 x 1, 2 x 2 at 2 CTAs/SM (FP64); 0: per-thread register
  *                 prefetch, per-term compensated sums.  Default: 2 for float,
  *                 bf16 hi/lo and bf16 hi-only history, 1 for double (the
  *                 fastest shapes measured on GB300 at 1024^2 x 4096).
@@ -367,12 +368,11 @@ typedef struct sbim_batch_ctx* sbim_batch;
  * (arrays of nb HOST values), one precision (SBIM_FP32 / BF16 variants), one
  * compensation flag and one stream.  The members are handles the batch owns
  * (reachable through sbim_batch_member).  A batch step runs the FFTs and the
- * epilogue per member and the history convolution of ALL members in one
- * persistent launch over their (member, orbit tile, 256-lag chunk) items, taken
- * from a work counter; each item writes its own partial sums, so results do not
- * depend on the schedule.  The batch sets its members' convolution launch
- * (sbim_set_conv_config) to the pipeline shape of the persistent kernel (3 for
- * float history, 1 for bf16) and 256 lags per chunk.
+ * epilogue per member and the history convolution of ALL members in one launch
+ * over their (member, orbit tile, lag chunk) work items; each item writes its
+ * own partial sums, so results do not depend on the schedule.  The batch sets
+ * its members' convolution launch (sbim_set_conv_config) to its own pipeline
+ * shape and 1024 lags per item (the default of sbim_batch_set_conv_config).
  */
 int sbim_batch_create(sbim_batch* out, int nb, const int* n1, const int* n3, const double* L1,
                       const double* L3, const double* cs, const double* cp, const double* rho,

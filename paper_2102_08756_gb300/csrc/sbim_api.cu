@@ -357,7 +357,7 @@ int choose_chunks(sbim_ctx& c) {
     c.lc = std::min(c.lags_per_cta, c.n_cut);
   } else {
     const long long tiles = c.n_orb_pad / (c.variant >= 1 ? c.tile : sbim::kOrbitTile);
-    const int per_sm = c.variant >= 1 ? sbim::conv_tma_ctas_per_sm(c.prec, c.variant, c.tile)
+    const int per_sm = c.variant >= 1 ? sbim::conv_tma_ctas_per_sm(c.prec, c.kahan, c.variant, c.tile)
                                       : (c.prec == SBIM_FP64 ? 1 : 3);
     const long long target = (long long)sms * per_sm * 16;
     long long S = (target + tiles - 1) / tiles;
@@ -682,7 +682,8 @@ int sbim_create(sbim_handle* out, int n1, int n3, double L1, double L3, double c
   c->stream = (cudaStream_t)stream;
   // default convolution launch: the shapes the autotuner measured fastest on
   // GB300 at 1024^2 x 4096 (shape 2 for every float-class history: 3 stages x
-  // 2 lags x 3 CTAs/SM, 6 x 2 x 3 for bf16 hi-only; 3 x 1 x 2 for double)
+  // 2 lags x 3 CTAs/SM, 6 x 2 x 3 for compensated bf16 hi-only and 6 x 1 x 5
+  // for uncompensated bf16 hi-only; 3 x 1 x 2 for double)
   c->variant = precision == SBIM_FP64 ? 1 : 2;
   const int rc = create_impl(c);
   if (rc != SBIM_OK) {

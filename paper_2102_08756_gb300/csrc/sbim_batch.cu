@@ -141,7 +141,7 @@ int configure(sbim_batch_ctx* b, int shape, int lags) {
   int dev = 0, sms = 148;
   BCU(cudaGetDevice(&dev));
   BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->shape, b->tile);
+  b->ctas = sms * sbim::conv_tma_ctas_per_sm(b->prec, b->kahan, b->shape, b->tile);
   return SBIM_OK;
 }
 

@@ -151,26 +151,44 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
   for (int g = 0; g < 4; ++g)
 #pragma unroll
     for (int k = 0; k < kFields; ++k) { sum[g][k] = (R)0; cmp[g][k] = (R)0; }
-  for (int ch = 0; ch < nch; ++ch) {
-    R x[4][kFields];
+  auto load_chunk = [&](int ch, R (&x)[4][kFields]) {
 #pragma unroll
     for (int g = 0; g < 4; ++g)
 #pragma unroll
       for (int k = 0; k < kFields; ++k)
         x[g][k] = part[((long long)ch * (4 * kFields) + g * kFields + k) * orb + o];
+  };
+  if constexpr (KAHAN) {
+    for (int ch = 0; ch < nch; ++ch) {
+      R x[4][kFields];
+      load_chunk(ch, x);
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
+      for (int g = 0; g < 4; ++g)
 #pragma unroll
-      for (int k = 0; k < kFields; ++k) {
-        if (KAHAN) {
+        for (int k = 0; k < kFields; ++k) {
           const R y = x[g][k] - cmp[g][k];
           const R t = sum[g][k] + y;
           cmp[g][k] = (t - sum[g][k]) - y;
           sum[g][k] = t;
-        } else {
-          sum[g][k] += x[g][k];
         }
-      }
+    }
+  } else if (nch > 0) {
+    // Plain sums: the next chunk's 40 loads are issued before this chunk's adds
+    // (left to the compiler, the uncompensated loop kept few loads in flight and
+    // ran at a third of the compensated one's rate on GB300).
+    R x[4][kFields];
+    load_chunk(0, x);
+    for (int ch = 0; ch < nch; ++ch) {
+      R xn[4][kFields];
+      if (ch + 1 < nch) load_chunk(ch + 1, xn);
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int k = 0; k < kFields; ++k) {
+          sum[g][k] += x[g][k];
+          x[g][k] = xn[g][k];
+        }
+    }
   }
 
   int pend = -1;

@@ -61,8 +61,10 @@ cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile, bool
   return dispatch(none, precision, kahan, shape, nullptr, nullptr, true, tile, halves);
 }
 
-int conv_tma_ctas_per_sm(int precision, int shape, int tile) {
-  const int minb = (precision == SBIM_FP64) ? 2 : (shape == 2 ? 3 : 2);
+int conv_tma_ctas_per_sm(int precision, int kahan, int shape, int tile) {
+  int minb = shape == 2 ? 3 : 2;   // FP32, BF16 hi/lo, compensated BF16 hi-only
+  if (precision == SBIM_FP64) minb = 2;
+  if (precision == SBIM_BF16 && !kahan) minb = shape == 1 ? 4 : (shape == 2 ? 5 : 3);
   return tma::minb_for_tile(minb, tile);
 }
 

@@ -88,7 +88,7 @@ cudaError_t launch_assemble_batch(const BatchLaunch& b, int total_tiles, int pre
 cudaError_t launch_conv_tma(const StepArgs& a, int precision, int kahan, int shape,
                             cudaStream_t s, const BatchLaunch* batch = nullptr,
                             int tile = kOrbitTile, bool halves = false);
-int conv_tma_ctas_per_sm(int precision, int shape, int tile = kOrbitTile);
+int conv_tma_ctas_per_sm(int precision, int kahan, int shape, int tile = kOrbitTile);
 // Set the shared-memory attributes of a shape's kernels (done before any launch,
 // so that launches can be captured in a CUDA graph).
 cudaError_t prepare_conv_tma(int precision, int kahan, int shape, int tile = kOrbitTile,
