@@ -42,15 +42,39 @@ struct Window {
   R v[3][3][3];
 };
 
+// Columns per CTA of the column march: kTX along x1 (one warp) by kTZ along x3,
+// one thread per (i1, i3) column.  Each node layer's values over the tile and a
+// one-node halo ([3][kHZ][kHX], periodic wrap) are staged in shared memory by
+// asynchronous copies, kStages layers deep, so a thread's 27-value window of a
+// layer is 27 shared-memory loads at constant offsets.
+constexpr int kTX = 32, kTZ = 4, kColThreads = kTX * kTZ;
+constexpr int kHX = kTX + 2, kHZ = kTZ + 2;
+constexpr int kLayerTile = 3 * kHZ * kHX;
+constexpr int kStages = 3;
+constexpr int kFillPer = (kLayerTile + kColThreads - 1) / kColThreads;
+
 template <class R>
-__device__ __forceinline__ void load_window(const R* __restrict__ xl, long long plane,
-                                            const long long (&q)[3][3], Window<R>& w) {
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(R))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <class R>
+__device__ __forceinline__ void load_window(const R* __restrict__ tile, int tz, int tx, Window<R>& w) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
-      for (int ox = 0; ox < 3; ++ox) w.v[c][oz][ox] = __ldg(xl + c * plane + q[oz][ox]);
+      for (int ox = 0; ox < 3; ++ox) w.v[c][oz][ox] = tile[(c * kHZ + tz + oz) * kHX + tx + ox];
 }
 
 // F += (-K) x from the element layer on one side of the node: side 0 (below)
@@ -80,72 +104,99 @@ __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>&
   }
 }
 
-// The stencil -K x for every node of one (i1, i3) column, marching up the node
-// layers with two register windows: at layer l one holds layer l-1 and the other
-// layer l; after the blocks below the node are applied, the first is reloaded
-// with layer l+1 for the blocks above, and the two swap roles for layer l+1.
-// Each layer of x is loaded once per column (27 values), not once per
-// neighbouring node layer.  A layer's element blocks below (down) and above (up)
-// exist unless they cross the split fault plane or the slab's faces.  Per node,
-// epi(l, q0, down, up, F) finishes.
+// The stencil -K x for every node of the CTA's kTX x kTZ columns, marching up
+// the node layers with two register windows: at layer l one holds layer l-1 and
+// the other layer l; after the blocks below the node are applied, the first is
+// refilled with layer l+1 (from shared memory) for the blocks above, and the two
+// swap roles for layer l+1.  The copy of layer l+2's tile starts as layer l
+// begins, into the buffer of layer l-1 (last read while layer l-2 was computed,
+// before the barrier of layer l-1), and is waited for one layer later.  A
+// layer's element blocks below (down) and above (up) exist unless they cross
+// the split fault plane or the slab's faces.  Per node of a column inside the
+// grid, epi(l, q0, down, up, F) finishes; threads of columns outside it still
+// copy and synchronise.
 template <class R, class Epi>
-__device__ __forceinline__ void stencil_column(const R* __restrict__ x, const MeshArgs& g,
-                                               const Stencil<R>& S, int i1, int i3, Epi epi) {
+__device__ __forceinline__ void stencil_columns(const R* __restrict__ x, const MeshArgs& g,
+                                                const Stencil<R>& S, Epi epi) {
+  __shared__ __align__(16) R tiles[kStages][kLayerTile];
+  const int tx = threadIdx.x % kTX, tz = threadIdx.x / kTX;
+  const int x0 = blockIdx.x * kTX, z0 = blockIdx.y * kTZ;
+  const int i1 = x0 + tx, i3 = z0 + tz;
+  const bool inside = i1 < g.n1 && i3 < g.n3;
   const long long plane = (long long)g.n1 * g.n3;
-  long long q[3][3];
-#pragma unroll
-  for (int oz = 0; oz < 3; ++oz) {
-    int j3 = i3 + oz - 1;
-    j3 += (j3 < 0) ? g.n3 : (j3 >= g.n3 ? -g.n3 : 0);
-#pragma unroll
-    for (int ox = 0; ox < 3; ++ox) {
-      int j1 = i1 + ox - 1;
-      j1 += (j1 < 0) ? g.n1 : (j1 >= g.n1 ? -g.n1 : 0);
-      q[oz][ox] = (long long)j3 * g.n1 + j1;
-    }
-  }
-  const long long q0 = (long long)i3 * g.n1 + i1;
   const long long layer = 3 * plane;
+  // this thread's share of a layer tile: tile index and in-layer source offset
+  int ti[kFillPer];
+  long long src[kFillPer];
+#pragma unroll
+  for (int k = 0; k < kFillPer; ++k) {
+    const int e = threadIdx.x + k * kColThreads;
+    ti[k] = e < kLayerTile ? e : -1;
+    const int c = e / (kHZ * kHX), r = (e / kHX) % kHZ, q = e % kHX;
+    const int j3 = ((z0 - 1 + r) % g.n3 + g.n3) % g.n3;
+    const int j1 = ((x0 - 1 + q) % g.n1 + g.n1) % g.n1;
+    src[k] = c * plane + (long long)j3 * g.n1 + j1;
+  }
+  auto fill = [&](int l) {
+    if (l < g.L) {
+      R* t = tiles[l % kStages];
+      const R* xl = x + (long long)l * layer;
+#pragma unroll
+      for (int k = 0; k < kFillPer; ++k)
+        if (ti[k] >= 0) cp_async_elem(t + ti[k], xl + src[k]);
+    }
+    cp_async_commit();   // an empty group past the top layer keeps the count uniform
+  };
+  const long long q0 = inside ? (long long)i3 * g.n1 + i1 : 0;
+  fill(0);
+  fill(1);
+  cp_async_wait<1>();    // layer 0 landed
+  __syncthreads();
+  Window<R> A, B;
+  load_window(tiles[0], tz, tx, B);
   int l = 0;
   auto node = [&](Window<R>& prev, Window<R>& cur) {
+    fill(l + 2);
     const bool down = l > 0 && !(g.fault && l == g.f + 1);
     const bool up = l < g.L - 1 && !(g.fault && l == g.f);
     R F[3] = {(R)0, (R)0, (R)0};
     if (down) apply_side<0>(S, prev, cur, F);
-    if (l + 1 < g.L) load_window(x + (l + 1) * layer, plane, q, prev);   // prev := layer l+1
+    cp_async_wait<1>();    // layer l+1 landed (layer l+2 may still be in flight)
+    __syncthreads();
+    if (l + 1 < g.L) load_window(tiles[(l + 1) % kStages], tz, tx, prev);   // prev := layer l+1
     if (up) apply_side<1>(S, cur, prev, F);
-    epi(l, q0, down, up, F);
+    if (inside) epi(l, q0, down, up, F);
     ++l;
   };
-  Window<R> A, B;
-  load_window(x, plane, q, B);
   while (l < g.L) {
     node(A, B);
     if (l >= g.L) break;
     node(B, A);
   }
+  cp_async_wait<0>();
 }
 
 // an = (-K u + f_boundary) / m: the acceleration without fault traction.
 // f_boundary = +A tau_top on the top layer, -A tau_bot on the bottom layer.
 template <class R>
-__global__ void __launch_bounds__(128) force_kernel(const R* __restrict__ u, R* __restrict__ an,
+__global__ void __launch_bounds__(kColThreads) force_kernel(const R* __restrict__ u, R* __restrict__ an,
                                                     MeshArgs g, const __grid_constant__ Stencil<R> S,
                                                     const R* __restrict__ tau_top,
                                                     const R* __restrict__ tau_bot,
                                                     const R* __restrict__ src) {
-  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i3 = blockIdx.y;
-  if (i1 >= g.n1) return;
   const long long plane = (long long)g.n1 * g.n3;
-  stencil_column(u, g, S, i1, i3, [&](int l, long long q0, bool down, bool up, R(&F)[3]) {
+  // 1 / lumped mass of a node with elements on both sides or on one (every node
+  // of a slab has elements on at least one side), converted and divided once
+  const R hm = (R)g.half_mass;
+  const R inv_m1 = (R)1 / hm, inv_m2 = (R)1 / (hm + hm);
+  stencil_columns(u, g, S, [&](int l, long long q0, bool down, bool up, R(&F)[3]) {
     if (l == g.L - 1 && tau_top)
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] += g.area * tau_top[c * plane + q0];
     if (l == 0 && tau_bot)
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] -= g.area * tau_bot[c * plane + q0];
-    const R inv_m = (R)1 / ((down ? (R)g.half_mass : (R)0) + (up ? (R)g.half_mass : (R)0));
+    const R inv_m = (down && up) ? inv_m2 : inv_m1;
     R* al = an + (long long)l * 3 * plane;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -356,14 +407,11 @@ __global__ void adj_mass_kernel(const R* __restrict__ laf, R* __restrict__ lF, M
 
 // out += -K x (the stiffness is symmetric: this is the transpose of -K u)
 template <class R>
-__global__ void __launch_bounds__(128) stiffness_add_kernel(const R* __restrict__ x,
+__global__ void __launch_bounds__(kColThreads) stiffness_add_kernel(const R* __restrict__ x,
                                                             R* __restrict__ out, MeshArgs g,
                                                             const __grid_constant__ Stencil<R> S) {
-  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i3 = blockIdx.y;
-  if (i1 >= g.n1) return;
   const long long plane = (long long)g.n1 * g.n3;
-  stencil_column(x, g, S, i1, i3, [&](int l, long long q0, bool, bool, R(&F)[3]) {
+  stencil_columns(x, g, S, [&](int l, long long q0, bool, bool, R(&F)[3]) {
     R* ol = out + (long long)l * 3 * plane + q0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) ol[c * plane] += F[c];
@@ -392,6 +440,10 @@ __global__ void adj_predict_kernel(const R* __restrict__ lun, const R* __restric
   }
 }
 
+dim3 column_grid(const MeshArgs& g) {
+  return dim3((unsigned)((g.n1 + kTX - 1) / kTX), (unsigned)((g.n3 + kTZ - 1) / kTZ));
+}
+
 unsigned grid1(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)(b > 152 * 32 ? 152 * 32 : b);
@@ -408,9 +460,7 @@ cudaError_t predict(R* u, R* v, const R* a, long long n, R dt, cudaStream_t st) 
 template <class R>
 cudaError_t force(const R* u, R* an, const MeshArgs& g, const Stencil<R>& S, const R* tau_top,
                   const R* tau_bot, const R* src, cudaStream_t st) {
-  const int tx = g.n1 >= 128 ? 128 : 32;
-  const dim3 grid((g.n1 + tx - 1) / tx, g.n3);
-  force_kernel<R><<<grid, tx, 0, st>>>(u, an, g, S, tau_top, tau_bot, src);
+  force_kernel<R><<<column_grid(g), kColThreads, 0, st>>>(u, an, g, S, tau_top, tau_bot, src);
   return cudaGetLastError();
 }
 
@@ -460,9 +510,7 @@ cudaError_t adjoint_stages(const AdjointArgs<R>& j, const MeshArgs& g, const Ste
       adj_mass_kernel<R><<<grid1(n, 256), 256, 0, st>>>(j.lan, j.lF, g, j.tb_top, j.tb_bot);
       break;
     case 4: {
-      const int tx = g.n1 >= 128 ? 128 : 32;
-      const dim3 grid((g.n1 + tx - 1) / tx, g.n3);
-      stiffness_add_kernel<R><<<grid, tx, 0, st>>>(j.lF, j.lun, g, S);
+      stiffness_add_kernel<R><<<column_grid(g), kColThreads, 0, st>>>(j.lF, j.lun, g, S);
       break;
     }
     case 5:
