@@ -29,8 +29,9 @@ struct Stencil {
 // so the block of a neighbour with no offset along x1 (ox == 1) couples the x1
 // component only with itself, and likewise for x3 (oz == 1): entry (c, d) of such
 // a block vanishes when exactly one of c, d is that axis (components 0 = x1,
-// 2 = x3).  88 of the 324 entries vanish; the assembly sets them to exactly 0 and
-// the kernels skip them.
+// 2 = x3).  88 of the 324 entries vanish; the assembly sets them to exactly 0.
+// (The column-march kernels use the symmetry itself: they read only the +x1 /
+// +x3 neighbours' coefficients, never a vanishing one.)
 __host__ __device__ constexpr bool stencil_entry_vanishes(int ox, int oz, int c, int d) {
   return (ox == 1 && ((c == 0) != (d == 0))) || (oz == 1 && ((c == 2) != (d == 2)));
 }

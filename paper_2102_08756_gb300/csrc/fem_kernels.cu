@@ -35,11 +35,19 @@ __global__ void predict_kernel(R* __restrict__ u, R* __restrict__ v, const R* __
   }
 }
 
-// One node layer of a field around a node: [component][oz][ox], the 3 x 3
-// in-plane neighbourhood (periodic in x1 and x3).
+// One node layer of a field around a node, the 3 x 3 in-plane neighbourhood
+// (periodic in x1 and x3) of each component d, held as the nine sums and
+// differences of mirrored neighbours that the stencil's mirror symmetry lets
+// share one coefficient: with x[oz][ox] the neighbour at offset (ox - 1, oz - 1),
+//   CC = x[1][1]                          centre
+//   XS, XD = x[1][2] +- x[1][0]           x1 neighbours
+//   ZS, ZD = x[2][1] +- x[0][1]           x3 neighbours
+//   SS, DS, SD, DD = corners, even/odd (S/D) in x1 then in x3:
+//     x[2][2] + sx x[2][0] + sz x[0][2] + sx sz x[0][0].
+enum { CC, XS, XD, ZS, ZD, SS, DS, SD, DD };
 template <class R>
 struct Window {
-  R v[3][3][3];
+  R k[3][9];
 };
 
 // Columns per CTA of the column march: kTX along x1 (one warp) by kTZ along x3,
@@ -67,22 +75,41 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// A layer's window from its shared-memory tile: 27 loads, 36 adds.
 template <class R>
 __device__ __forceinline__ void load_window(const R* __restrict__ tile, int tz, int tx, Window<R>& w) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int d = 0; d < 3; ++d) {
+    R x[3][3];
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
-      for (int ox = 0; ox < 3; ++ox) w.v[c][oz][ox] = tile[(c * kHZ + tz + oz) * kHX + tx + ox];
+      for (int ox = 0; ox < 3; ++ox) x[oz][ox] = tile[(d * kHZ + tz + oz) * kHX + tx + ox];
+    const R p = x[2][2] + x[2][0], m = x[2][2] - x[2][0];
+    const R q = x[0][2] + x[0][0], r = x[0][2] - x[0][0];
+    w.k[d][CC] = x[1][1];
+    w.k[d][XS] = x[1][2] + x[1][0];
+    w.k[d][XD] = x[1][2] - x[1][0];
+    w.k[d][ZS] = x[2][1] + x[0][1];
+    w.k[d][ZD] = x[2][1] - x[0][1];
+    w.k[d][SS] = p + q;
+    w.k[d][DS] = m + r;
+    w.k[d][SD] = p - q;
+    w.k[d][DD] = m - r;
+  }
 }
 
 // F += (-K) x from the element layer on one side of the node: side 0 (below)
-// spans node layers l-1 (lo) and l (hi), side 1 (above) layers l and l+1.  Fully
-// unrolled: every stencil index is a compile-time constant, and the stencil holds
-// -K so that each entry is one fused multiply-add.  The entries that vanish by
-// symmetry (stencil_entry_vanishes) are skipped: 236 multiply-adds per node
-// instead of 324.
+// spans node layers l-1 (lo) and l (hi), side 1 (above) layers l and l+1.  The
+// four elements on one side of a node are mirror-symmetric in x1 and x3, so
+// block (c, d) of the neighbour at -x1 equals sx times that at +x1, with
+// sx = -1 when exactly one of c, d is the x1 component (likewise sz for x3; the
+// assembled stencil holds these equalities to rounding, exactly in float).  Each
+// block (c, d) therefore takes the +x1 / +x3 neighbours' coefficients times the
+// window's sums (even) or differences (odd): 4, 2, 2 or 1 multiply-adds for
+// (sx, sz) = (+, +), (-, +), (+, -), (-, -); 88 per node instead of the 236
+// nonzero stencil entries.  Fully unrolled; the stencil holds -K and reaches
+// the kernel by value, so every coefficient is a constant-bank operand.
 template <int SIDE, class R>
 __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>& lo,
                                            const Window<R>& hi, R (&F)[3]) {
@@ -90,16 +117,26 @@ __device__ __forceinline__ void apply_side(const Stencil<R>& S, const Window<R>&
   for (int oy = 0; oy < 2; ++oy) {
     const Window<R>& w = oy == 0 ? lo : hi;
 #pragma unroll
-    for (int oz = 0; oz < 3; ++oz)
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int ox = 0; ox < 3; ++ox) {
-        const int s = SIDE * 18 * 9 + ((ox * 2 + oy) * 3 + oz) * 9;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            if (!stencil_entry_vanishes(ox, oz, c, d))
-              F[c] = fma(S.s[s + 3 * c + d], w.v[d][oz][ox], F[c]);
+      for (int d = 0; d < 3; ++d) {
+        // coefficient of the neighbour at (ox, oz) in block (c, d)
+        auto co = [&](int ox, int oz) { return S.s[SIDE * 18 * 9 + ((ox * 2 + oy) * 3 + oz) * 9 + 3 * c + d]; };
+        const bool odd_x = (c == 0) != (d == 0), odd_z = (c == 2) != (d == 2);
+        if (!odd_x && !odd_z) {
+          F[c] = fma(co(1, 1), w.k[d][CC], F[c]);
+          F[c] = fma(co(2, 1), w.k[d][XS], F[c]);
+          F[c] = fma(co(1, 2), w.k[d][ZS], F[c]);
+          F[c] = fma(co(2, 2), w.k[d][SS], F[c]);
+        } else if (odd_x && !odd_z) {
+          F[c] = fma(co(2, 1), w.k[d][XD], F[c]);
+          F[c] = fma(co(2, 2), w.k[d][DS], F[c]);
+        } else if (!odd_x && odd_z) {
+          F[c] = fma(co(1, 2), w.k[d][ZD], F[c]);
+          F[c] = fma(co(2, 2), w.k[d][SD], F[c]);
+        } else {
+          F[c] = fma(co(2, 2), w.k[d][DD], F[c]);
+        }
       }
   }
 }
