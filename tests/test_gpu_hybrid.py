@@ -81,6 +81,39 @@ def test_linear_slab_matches_oracle(precision, tol, fault, boundaries):
     g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 5e-6)])
+@pytest.mark.parametrize("n1,n3", [(40, 10), (64, 6)])
+def test_force_tiles_with_ragged_edges(precision, tol, n1, n3):
+    """The force kernel marches columns in tiles of 32 x 4 with a periodic halo:
+    grids that span several tiles with a ragged last one in x1 (40) or x3 (10,
+    6) and wrap across tile edges, with a split plane and both half-spaces,
+    equal the oracle after 20 steps."""
+    from paper_2102_08756_gb300.hybrid import Hybrid
+    n2, h, n_cut, steps = 4, 50.0, 12, 20
+    dt = 0.3 * h / CP
+    me = SlabMesh(n1, n2, n3, h, fault=True)
+    o = HybridOracle(me, CS, CP, RHO, dt, n_cut=n_cut, sbim=True)
+    rng = np.random.default_rng(5)
+    o.u = rng.normal(size=o.u.shape) * 1e-3
+    o.v = rng.normal(size=o.u.shape) * 1e-2
+    o.u[me.f + 1] = o.u[me.f]
+    o.v[me.f + 1] = o.v[me.f]
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    g = Hybrid(n1, n2, n3, h, CS, CP, RHO, dt, n_cut, precision, True, True)
+    g.set_state(torch.from_numpy(o.u).to("cuda", dtype), torch.from_numpy(o.v).to("cuda", dtype),
+                None)
+    for _ in range(steps):
+        o.step()
+        g.step()
+    u, v, a = (assert_finite(x.double().cpu().numpy(), "state") for x in g.get_state())
+    print(f"\nTILES-REPORT {precision} {n1}x{n3}: relative L2 error u {rel(u, o.u):.3e} "
+          f"v {rel(v, o.v):.3e} a {rel(a, o.a):.3e}")
+    assert rel(u, o.u) < tol
+    assert rel(v, o.v) < tol
+    assert rel(a, o.a) < tol
+    g.close()
+
+
 def _rupture_setup(n1, n3):
     i3, i1 = np.meshgrid(np.arange(n3), np.arange(n1), indexing="ij")
     patch = (np.abs(i1 - n1 / 2 + 0.5) < 3) & (np.abs(i3 - n3 / 2 + 0.5) < 3)
