@@ -104,7 +104,9 @@ int sbim_step(sbim_handle h, const void* u, const void* v, void* tau);
 /*
  * sbim_step_host -- as sbim_step, with u, v, tau in HOST memory (pageable or
  * pinned).  Copies the inputs to device work buffers, runs the step, copies
- * tau back and waits for the stream.  Section 2.4 step 2 (displacement and
+ * tau back and waits for the stream; the device error word comes back with tau
+ * and is checked as by sbim_check_device (SBIM_ERR_TIMEOUT if a bounded wait
+ * gave up).  Section 2.4 step 2 (displacement and
  * predicted velocity handed from FE to SBI) for a caller whose FE solver runs on the
  * host.  The convolution over lags >= 1 (which needs only the stored history)
  * runs while the inputs are copied and transformed on a side stream; the lag-0

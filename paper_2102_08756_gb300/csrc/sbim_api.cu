@@ -141,6 +141,7 @@ struct sbim_ctx {
   double window = 0.0;
   std::vector<double> h_dT;   // |k| c_s dt per half record, [o][2] (host copy)
   void* d_io = nullptr;  // u, v, tau staging and zero spectra for sbim_step_host
+  int* h_err = nullptr;  // pinned copy of the error word, read with tau by sbim_step_host
   cudaStream_t io_stream = nullptr;          // sbim_step_host: copies in + forward FFT
   cudaEvent_t io_fork = nullptr, io_join = nullptr;
   cufftHandle plan_fwd = 0, plan_inv = 0;
@@ -399,6 +400,7 @@ void release(sbim_ctx* c) {
   if (c->io_fork) cudaEventDestroy(c->io_fork);
   if (c->io_join) cudaEventDestroy(c->io_join);
   if (c->io_stream) cudaStreamDestroy(c->io_stream);
+  if (c->h_err) cudaFreeHost(c->h_err);
   delete c;
 }
 
@@ -779,6 +781,17 @@ int run_step(sbim_ctx* c, const void* in, const void* aux, void* out, bool adjoi
   return SBIM_OK;
 }
 
+// The device error word as read after the stream drained: clears it and
+// reports SBIM_ERR_TIMEOUT when a bounded wait gave up.
+int take_error_word(sbim_ctx* c, int flag) {
+  if (flag) {
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    return fail(SBIM_ERR_TIMEOUT, "a bounded device wait gave up; the outputs since the last check "
+                                  "are invalid");
+  }
+  return SBIM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -812,6 +825,7 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
   sbim_ctx* c = h;
   const size_t bytes = c->field_elems() * c->real_size;
   const size_t hat_bytes = (size_t)3 * c->nbins * 2 * c->real_size;
+  if (!c->h_err) CU(cudaHostAlloc((void**)&c->h_err, sizeof(int), cudaHostAllocDefault));
   if (!c->d_io) {
     CU(cudaMalloc(&c->d_io, 3 * bytes + hat_bytes));
     CU(cudaMemsetAsync((char*)c->d_io + 3 * bytes, 0, hat_bytes, c->stream));
@@ -862,9 +876,11 @@ int sbim_step_host(sbim_handle h, const void* u, const void* v, void* tau) {
     ++c->n;
     c->can_repeat = true;
   }
+  // tau and the device error word come back under one synchronisation
   CU(cudaMemcpyAsync(tau, dtau, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  return sbim_check_device(h);
+  return take_error_word(c, *c->h_err);
 }
 
 int sbim_set_window(sbim_handle h, double window) {
@@ -907,12 +923,7 @@ int sbim_check_device(sbim_handle h) {
   int flag = 0;
   CU(cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
-  if (flag) {
-    CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-    return fail(SBIM_ERR_TIMEOUT, "a bounded device wait gave up; the outputs since the last check "
-                                  "are invalid");
-  }
-  return SBIM_OK;
+  return take_error_word(h, flag);
 }
 
 int sbim_selftest_wait_timeout(sbim_handle h) {
