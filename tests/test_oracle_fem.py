@@ -1,6 +1,7 @@
 """Pins of the FEM / fault / coupling oracle (Sections 2.1, 2.2, 2.4): the
 element stiffness against closed-form strain energies and rigid-body modes,
-mass conservation, energy conservation of free vibration, a welded split plane
+the mirror symmetry of the assembled stiffness in x1 and x3, mass
+conservation, energy conservation of free vibration, a welded split plane
 against the unsplit mesh, the linear slip-weakening law, a pulse that leaves
 through the SBIM boundaries without reflection, independence of the fault
 solution from the strip width (the paper's own validation), and the energy
@@ -38,6 +39,28 @@ def test_element_stiffness_strain_energy_and_rigid_modes():
         assert np.abs(K @ (x @ W.T).ravel()).max() < 1e-8 * np.abs(K).max() * h
     ev = np.linalg.eigvalsh(K)
     assert np.sum(ev < 1e-9 * ev.max()) == 6
+
+
+def test_stiffness_is_mirror_equivariant_in_x1_and_x3():
+    """K u on the periodic slab commutes with the mirrors x1 -> -x1 (the x1
+    component of u changing sign) and x3 -> -x3 (likewise x3), on either side of
+    a split plane: the symmetry of the 8-node elements that lets a column-march
+    stencil share one coefficient between mirrored neighbours (sums for the
+    even component pairs, differences for the odd ones)."""
+    me = SlabMesh(6, 4, 8, 10.0, fault=True)
+    fem = FEMOracle(me, CS, CP, RHO)
+    rng = np.random.default_rng(11)
+    u = rng.normal(size=(me.layers, 3, me.n3, me.n1))
+    Ku = fem.internal_force(u)
+    for axis, comp in ((3, 0), (2, 2)):        # array axis of x1 / x3, their component
+        def mirror(f):
+            g = np.flip(f, axis=axis)
+            g = np.roll(g, 1, axis=axis)        # i -> (-i) mod n on the periodic grid
+            g = g.copy()
+            g[:, comp] *= -1.0
+            return g
+        got = fem.internal_force(mirror(u))
+        np.testing.assert_allclose(got, mirror(Ku), rtol=0, atol=1e-12 * np.abs(Ku).max())
 
 
 def test_lumped_mass_total():
