@@ -172,22 +172,34 @@ __device__ __forceinline__ void assemble_orbit(const StepArgs& a, int o) {
           sum[g][k] = t;
         }
     }
-  } else if (nch > 0) {
-    // Plain sums: the next chunk's 40 loads are issued before this chunk's adds
-    // (left to the compiler, the uncompensated loop kept few loads in flight and
-    // ran at a third of the compensated one's rate on GB300).
-    R x[4][kFields];
-    load_chunk(0, x);
+  } else if constexpr (sizeof(R) == 8) {
+    // FP64 sums (their step is bound by the FP64 pipe): one chunk at a time
     for (int ch = 0; ch < nch; ++ch) {
-      R xn[4][kFields];
-      if (ch + 1 < nch) load_chunk(ch + 1, xn);
+      R x[4][kFields];
+      load_chunk(ch, x);
 #pragma unroll
       for (int g = 0; g < 4; ++g)
 #pragma unroll
-        for (int k = 0; k < kFields; ++k) {
-          sum[g][k] += x[g][k];
-          x[g][k] = xn[g][k];
-        }
+        for (int k = 0; k < kFields; ++k) sum[g][k] += x[g][k];
+    }
+  } else if (nch > 0) {
+    // Plain float sums: the next chunk's 40 loads are issued before this chunk's
+    // adds (left to the compiler, the uncompensated loop kept few loads in flight
+    // and ran at a third of the compensated one's rate on GB300).
+    R x[4][kFields], xn[4][kFields];
+    load_chunk(0, x);
+    for (int ch = 0; ch < nch; ++ch) {
+      const bool more = ch + 1 < nch;
+      if (more) load_chunk(ch + 1, xn);
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int k = 0; k < kFields; ++k) sum[g][k] += x[g][k];
+      if (more)
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+          for (int k = 0; k < kFields; ++k) x[g][k] = xn[g][k];
     }
   }
 
