@@ -24,7 +24,7 @@ def built():
     __graft_entry__.build()
 
 
-def _setup(stream):
+def _setup(stream, precision=1, kahan=1):
     from paper_2102_08756_gb300 import sbim as B
     dx = 100.0
     dt = 0.3 * dx / CP
@@ -32,7 +32,7 @@ def _setup(stream):
     n3 = [m[1] for m in MEMBERS]
     b = B.sbim_batch_create(n1, n3, [x * dx for x in n1], [x * dx for x in n3], [CS] * 5, [CP] * 5,
                             [RHO] * 5, [dt] * 5, [m[2] for m in MEMBERS], [m[3] for m in MEMBERS],
-                            1, 1, stream.cuda_stream)
+                            precision, kahan, stream.cuda_stream)
     hist = [separable_history(a, c, a * dx, c * dx, 80, dt, CS, seed=10 + k, spectrum="k2")
             for k, (a, c, _, _) in enumerate(MEMBERS)]
     return B, b, hist, dt
@@ -87,6 +87,54 @@ def test_batch_equals_members_stepped_alone(shape, lags, tile):
                 for c in range(3):
                     if np.linalg.norm(r[c]) > 0:
                         assert np.linalg.norm(got[c] - r[c]) / np.linalg.norm(r[c]) < 1e-5
+        for h in alone:
+            h.check()
+            h.close()
+        for k in range(len(MEMBERS)):
+            B.sbim_check_device(B.sbim_batch_member(b, k))
+        B.sbim_batch_destroy(b)
+
+
+@pytest.mark.parametrize("shape,lags", [(None, None), (4, 1024), (5, 256)])
+def test_bf16_batch_equals_members_stepped_alone(shape, lags):
+    """Uncompensated BF16 hi-only history (SBIM_BF16, whose pipeline shapes are
+    1-lag stages at 4 and 5 CTAs per SM): the default batch launch (persistent
+    CTAs, shape 1, 1024-lag items) and one CTA per item (shapes 1 and 2) equal
+    the members stepped alone with the same shape and lag chunking, bit for bit,
+    and stay within the BF16 hi-only bound (1e-2) of the oracle."""
+    from paper_2102_08756_gb300.sbim import SBIM
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        B, b, hist, dt = _setup(stream, precision=3, kahan=0)
+        if shape is not None:
+            B.sbim_batch_set_conv_config(b, shape, lags)
+        alone = []
+        for (a, c, n_cut, side) in MEMBERS:
+            h = SBIM(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side, "bf16", False,
+                     stream=stream)
+            if shape is None:
+                h.set_conv_config(1, 1024)
+            else:
+                h.set_conv_config(shape - 3 if shape > 3 else shape, lags)
+            alone.append(h)
+        oracles = [SBIMOracle(a, c, a * 100.0, c * 100.0, CS, CP, RHO, dt, n_cut, side)
+                   for (a, c, n_cut, side) in MEMBERS[:2]]
+        for m in range(60):
+            u, v = _fields(hist, m)
+            tau = [torch.empty_like(x) for x in u]
+            B.sbim_batch_step(b, [x.data_ptr() for x in u], [x.data_ptr() for x in v],
+                              [x.data_ptr() for x in tau])
+            ref = [alone[k].step(u[k], v[k]) for k in range(len(MEMBERS))]
+            stream.synchronize()
+            for k in range(len(MEMBERS)):
+                assert_finite(tau[k], "batched tau")
+                assert torch.equal(tau[k], ref[k]), (m, k)
+            for k, o in enumerate(oracles):
+                r = o.step(u[k].double().cpu().numpy(), v[k].double().cpu().numpy())["tau"]
+                got = tau[k].double().cpu().numpy()
+                for c in range(3):
+                    if np.linalg.norm(r[c]) > 0:
+                        assert np.linalg.norm(got[c] - r[c]) / np.linalg.norm(r[c]) < 1e-2
         for h in alone:
             h.check()
             h.close()
