@@ -202,3 +202,44 @@ def test_fault_solver_restart_is_bit_exact(symmetric):
         b.step()
         assert torch.equal(b.fault_fields()[1].cpu(), r)
     assert float(ref[-1].abs().max()) > 0.1
+
+
+@pytest.mark.parametrize("precision,rec_bytes", [("fp32", 32), ("fp64", 64)])
+@pytest.mark.parametrize("variant", [2, 0])
+def test_nan_canaries_in_padding_records_never_reach_the_output(precision, rec_bytes, variant):
+    """NaN canaries in padding: the record tiles are padded to whole tiles of 128
+    records whose member slots hold no Fourier bin.  A checkpoint whose ring
+    holds NaN in every padding record, of every slot and component, is loaded;
+    the following steps (the convolution reads those records every lag) give the
+    same tractions, bit for bit, as a handle that never saw them.  Ring layout
+    of one precision plane: [slot][component][record] records of 4 members."""
+    from tests._layout import grid_records
+    n1, n3, n_cut, split, steps = 16, 16, 12, 15, 25
+    dt = 0.3 * 100.0 / CP
+    hist = separable_history(n1, n3, 100.0 * n1, 100.0 * n3, steps, dt, CS, seed=9)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    fields = [(torch.from_numpy(hist.u(m)).to("cuda", tdt), torch.from_numpy(hist.v(m)).to("cuda", tdt))
+              for m in range(steps)]
+    a, b = _make(n1, n3, n_cut, precision), _make(n1, n3, n_cut, precision)
+    for h in (a, b):
+        h.set_conv_config(variant, 0)
+    for m in range(split):
+        a.step(*fields[m])
+        b.step(*fields[m])
+    ck = a.save()
+    info = a.info()
+    n_pad = info["n_slots"] // 4
+    n_rec = len(grid_records(n1, n3, 100.0 * n1, 100.0 * n3)[0])
+    assert n_pad > n_rec                                   # the grid has padding records
+    head = ck.size - info["hist_bytes"]
+    ring = ck[head:].view(np.float32 if precision == "fp32" else np.float64)
+    ring = ring.reshape(n_cut, 3, n_pad, rec_bytes // ring.itemsize)
+    ring[:, :, n_rec:, :] = np.nan
+    a.load(ck)
+    for m in range(split, steps):
+        x = a.step(*fields[m]).cpu().numpy()
+        y = b.step(*fields[m]).cpu().numpy()
+        assert np.isfinite(x).all(), m
+        assert np.array_equal(x, y), m
+    a.check()
+    b.check()
